@@ -1,0 +1,195 @@
+/*
+ * morph.h -- C ABI of the GB300 (sm_103a) library for exact grey-value
+ * dilation and erosion by umbra / polynomial convolution.
+ *
+ * Method (arxiv 2305.03018, Sec. 3): every pixel value f(x) becomes the
+ * monomial t^f(x) (Step 1, Eq. 7), every structuring-element value b(y)
+ * becomes t^b(y) (Eq. 8); their full-mode convolution over space x grey level
+ * (Step 2) gives at each pixel a polynomial with non-negative integer
+ * coefficients -- the number of SE taps y with f(x - y) + b(y) = d (Eq. Obs7)
+ * -- and the dilation is the degree of its highest nonzero coefficient
+ * (Step 3, Eq. 9).  Erosion is computed through duality (Sec. 2.1):
+ * f (-) b = (L - 1) - ((L - 1 - f) (+) b_reflected).
+ *
+ * Conventions shared by every call:
+ *   - Image f: N images of H x W pixels, integer values in [0, L-1]
+ *     (Sec. 2.1, tonal range {0..l}, L = l + 1).  Device memory.
+ *   - SE b on a kh x kw box; box entry (r, c) is the spatial offset
+ *     y = (r - oy, c - ox).  mask[r*kw + c] != 0 puts y in B; offset[] gives
+ *     b(y) >= 0 (Sec. 2.1 requires b >= 0).  Host memory, read during the
+ *     call only.
+ *   - Dilation output (Eq. 6): D(x) = max{f(x-y) + b(y) : x-y in F, y in B},
+ *     0 where no tap is valid; int32, never clamped, in [0, L-1+max b].
+ *   - Erosion output (Eq. Erosion): min{f(x+y) - b(y) : x+y in F, y in B},
+ *     L-1 where no tap is valid; int32, never clamped, in [-max b, L-1].
+ *   - Optional top count: the coefficient of the top degree, i.e. how many
+ *     valid taps attain the result (0 where no tap is valid).
+ *   - Outputs are int32 [N][H][W], contiguous, device memory, owned by the
+ *     caller.  The library owns its context: plans, device workspace, the
+ *     device error word.
+ *   - Every call is stream-ordered and asynchronous unless stated otherwise.
+ *     Calls return a status synchronously for argument errors; data errors
+ *     found on the device (a pixel outside [0, L)) are reported by
+ *     morph_stream_check().
+ *   - A context is bound to one device and is not thread-safe: use one
+ *     context per host thread.
+ */
+#ifndef MORPH_H
+#define MORPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t / CUstream; NULL is the legacy default stream. */
+typedef struct CUstream_st *morph_stream_t;
+
+typedef struct morph_ctx morph_ctx;
+
+/* ------------------------------------------------------------- status */
+enum morph_status {
+    MORPH_OK = 0,
+    MORPH_E_INVAL = 1,       /* bad argument: shape, stride, L, SE, pointer */
+    MORPH_E_RANGE = 2,       /* data error found on the device (pixel not in [0, L)) */
+    MORPH_E_NOMEM = 3,       /* device or host allocation failed */
+    MORPH_E_PRECISION = 4,   /* FP32 FFT requested but its round-off bound fails */
+    MORPH_E_CUDA = 5,        /* a CUDA runtime/driver call failed */
+    MORPH_E_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    MORPH_E_UNSUPPORTED = 7  /* valid request outside what this build implements */
+};
+
+/* ------------------------------------------------------------- inputs */
+enum morph_dtype { MORPH_U8 = 0, MORPH_U16 = 1, MORPH_I32 = 2 };
+
+typedef struct {
+    const void *data;        /* device pointer to pixel (0,0) of image 0 */
+    int dtype;               /* enum morph_dtype */
+    int n, h, w;             /* images, rows, columns (each >= 1) */
+    int64_t row_stride;      /* elements between rows (>= w) */
+    int64_t batch_stride;    /* elements between images (>= h * row_stride) */
+    int L;                   /* number of grey levels, 2 <= L <= 256 */
+} morph_image;
+
+typedef struct {
+    int kh, kw;              /* box size, 1..63 each */
+    int oy, ox;              /* box entry of the spatial origin (any integers) */
+    const uint8_t *mask;     /* host, kh*kw, row-major */
+    const int32_t *offset;   /* host, kh*kw, >= 0 where mask != 0 */
+} morph_se;
+
+/* ------------------------------------------------------------ options */
+enum morph_method {
+    MORPH_AUTO = 0,          /* planner picks the fastest exact back-end */
+    MORPH_DIRECT_FP8 = 1,    /* tcgen05 FP8 implicit GEMM, exact by construction */
+    MORPH_FFT_F32 = 2,       /* FP32 FFT; refused (E_PRECISION) if the bound fails */
+    MORPH_FFT_F64 = 3        /* FP64 FFT, the plain form of the paper's Step 2 */
+};
+
+enum morph_flags {
+    MORPH_F_ALLOW_UNPROVEN_F32 = 1,  /* run FFT_F32 even where the a-priori bound fails */
+    MORPH_F_VALIDATE = 2             /* FFT routes: measure max |C - rint C| over every degree */
+};
+
+typedef struct {
+    int method;              /* enum morph_method */
+    int flags;               /* enum morph_flags, or-ed */
+    float *count_err;        /* device, nullable: FFT routes write max |C - rint C| seen */
+} morph_opts;
+
+/* What the planner chose for one problem (morph_plan_query). */
+typedef struct {
+    int method;              /* enum morph_method actually used */
+    int R;                   /* number of degrees: L + max b */
+    int taps;                /* |B| */
+    double f32_bound;        /* a-priori bound on the FP32 FFT count error */
+    double f64_bound;        /* the same bound for FP64 */
+    int fft_nx, fft_ny;      /* FFT sizes of the FFT routes */
+    int groups, passes;      /* direct route: offset levels stacked per pass, passes */
+    int tile_w, tile_h;      /* direct route: output tile (columns x rows) */
+    double est_flop;         /* issued dense FLOP (direct) or FFT FLOP (FFT routes) */
+    size_t workspace_bytes;  /* device workspace the call needs */
+} morph_plan_info;
+
+/* --------------------------------------------------------------- calls */
+
+/* Create a context on `device` (the CUDA ordinal).  The call makes `device`
+ * current on the calling thread.  Returns MORPH_OK and *out, or an error. */
+int morph_ctx_create(int device, morph_ctx **out);
+
+/* Wait for the context's work, release its device memory and free it. */
+int morph_ctx_destroy(morph_ctx *ctx);
+
+/* Plan (without running) the dilation (op = 0) or erosion (op = 1) of `f` by
+ * `b` under `opts` (nullable = AUTO).  Host-only except for a device query. */
+int morph_plan_query(morph_ctx *ctx, const morph_image *f, const morph_se *b, int op,
+                     const morph_opts *opts, morph_plan_info *out);
+
+/* Dilation, Eq. 6 (Steps 1-3 of Sec. 3).  out: int32 [n][h][w] device;
+ * out_count: nullable int32 [n][h][w] device, the top coefficient.
+ * The first call for a new (SE, L, shape, method) builds and caches a plan,
+ * which may allocate device memory and synchronize the device. */
+int morph_dilate(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_t *out,
+                 int32_t *out_count, const morph_opts *opts, morph_stream_t stream);
+
+/* Erosion, Eq. Erosion, by the duality of Sec. 2.1.  Arguments as morph_dilate;
+ * out_count counts the taps attaining the minimum. */
+int morph_erode(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_t *out,
+                int32_t *out_count, const morph_opts *opts, morph_stream_t stream);
+
+/* Backward of the dilation for a learnable layer.  The upstream gradient
+ * g = grad_out (fp32 [n][h][w], device) at x is routed to every tap attaining
+ * the maximum, split equally among the cD(x) of them:
+ *   grad_in(p)  = sum_{y in B, p+y in F, f(p)+b(y) = D(p+y)} g(p+y) / cD(p+y)
+ *   grad_se(y)  = sum_{x in F, x-y in F, f(x-y)+b(y) = D(x)} g(x) / cD(x),
+ * the latter being the coefficient of t^b(y) in the lag-y cross-correlation
+ * of g/cD * t^D with t^-f.  D and cD are the forward outputs (device int32).
+ * grad_in: nullable fp32 [n][h][w] device (overwritten).  grad_se: nullable
+ * fp32 [kh][kw] device (overwritten; 0 outside B).  Deterministic: fixed
+ * summation order, no atomics on floating point. */
+int morph_dilate_backward(morph_ctx *ctx, const morph_image *f, const morph_se *b,
+                          const int32_t *D, const int32_t *cD, const float *grad_out,
+                          float *grad_in, float *grad_se, morph_stream_t stream);
+
+/* One problem of a heterogeneous batch. */
+typedef struct {
+    morph_image f;
+    morph_se se;
+    int op;                  /* 0 = dilation, 1 = erosion */
+    int32_t *out;            /* device int32 [n][h][w] */
+    int32_t *out_count;      /* nullable */
+} morph_problem;
+
+/* Run `n` problems: all FP8-direct problems in one persistent launch, FFT
+ * problems after it, on `stream`.  Plans are built on first use. */
+int morph_run_batch(morph_ctx *ctx, const morph_problem *p, int n, const morph_opts *opts,
+                    morph_stream_t stream);
+
+typedef struct morph_batch morph_batch;
+
+/* Plan the batch once and capture its launches into a CUDA graph.  The
+ * problems' device pointers are baked into the graph: replays read the
+ * current contents of the same buffers. */
+int morph_batch_capture(morph_ctx *ctx, const morph_problem *p, int n, const morph_opts *opts,
+                        morph_batch **out);
+int morph_batch_launch(morph_batch *b, morph_stream_t stream);
+int morph_batch_destroy(morph_batch *b);
+
+/* Synchronize `stream`, then return (and clear) the device error word:
+ * MORPH_E_RANGE for a pixel outside [0, L), MORPH_E_TIMEOUT if a bounded wait
+ * gave up, MORPH_OK otherwise. */
+int morph_stream_check(morph_ctx *ctx, morph_stream_t stream);
+
+/* Static text for a status code. */
+const char *morph_strerror(int status);
+
+/* Number of kernel launches the library issued through this context since
+ * creation (every launch, every route). */
+uint64_t morph_launch_count(const morph_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MORPH_H */

@@ -1,0 +1,516 @@
+// Step 2 + Step 3 of the method (Sec. 3) on the 5th-generation tensor cores.
+//
+// Step 2 convolves the umbras: the count polynomial at pixel x has, at
+// degree d, the number of SE taps y with f(x - y) + b(y) = d (Eq. Obs7).
+// Split the taps by their offset level w = b(y): with
+//     H_w(x, v) = #{ y in B : b(y) = w, x - y in F, f(x - y) = v }
+// the polynomial is p_x(t) = sum_w t^w H_w(x, t).  All coefficients are
+// non-negative, so by the degree rules of Prop. 2.3 (deg(p q) = deg p +
+// deg q, deg(p + q) = max) Step 3 (Eq. 9) is
+//     D(x) = max_w ( w + top{v : H_w(x, v) >= 1} ),
+// and the top coefficient is the sum of H_w(x, D(x) - w) over the w that
+// attain that maximum.
+//
+// H_w is a sum of one-hot level vectors over shifted pixels, computed as a
+// dense FP8 GEMM per SE row r (exact: 0/1 operands, FP32 accumulation of
+// counts <= |B| < 2^24):
+//     acc[(g, j), (t, v)] += sum_k  T_r[(g, j), k] * U[i0 + t - (r - oy)][v][s + k]
+//   A = T_r : 128 x K Toeplitz of SE row r; row (g, j) holds a 1 at
+//             k = j + (kw - 1) - c for every tap (r, c) of offset group g;
+//   B = U   : the FP8 indicator planes (Step 1, Eq. 7), rows (t, v) = image
+//             row x grey level, K = a window of image columns;
+//   D       : 128 x 256 FP32 accumulator in TMEM.
+// M = 128 stacks G offset groups x J = 128 / G output columns, N = 256
+// stacks rows_n image rows x Lpad levels.  The epilogue reads a lane per
+// (group, column), finds each group's top level by a descending scan and
+// combines groups with (max, sum-at-max).
+//
+// Warp roles (192 threads, one persistent CTA per SM):
+//   warp 0   : TMA producer (one lane) -- A and B tiles into a 4-stage ring;
+//   warp 1   : TMEM allocator + MMA issuer (one lane), tcgen05.mma kind::f8f6f4;
+//   warps 2-5: epilogue (TMEM -> registers -> SMEM reduction -> int32 output).
+// Two TMEM accumulators (2 x 256 columns) let the epilogue of one unit
+// overlap the MMAs of the next.
+#include <algorithm>
+#include <cstring>
+
+#include "morph_internal.h"
+#include "ptx.cuh"
+
+namespace morph {
+
+constexpr int kStages = 4;
+constexpr int kStageA = 128 * 128;             // 16 KB: 128 Toeplitz rows x 128 B of K
+constexpr int kStageB = kDirectN * 128;        // 32 KB: 256 (row, level) rows x 128 B of K
+constexpr int kStageBytes = kStageA + kStageB;
+constexpr int kRedEntries = 16 * 128;          // rows_n (<= 16) x 128 lanes
+constexpr int kRunEntries = 2048;              // rows_n x J  (= 256 / Lpad * 128 / G <= 2048)
+constexpr int kDirectThreads = 192;
+constexpr uint32_t kTmemCols = 2 * kDirectN;   // two accumulators
+
+struct DirectSmemTail {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+int direct_stages() { return kStages; }
+int direct_smem_bytes(int stages) {
+    return 1024 + stages * kStageBytes + (kRedEntries + kRunEntries) * 8 + static_cast<int>(sizeof(DirectSmemTail));
+}
+
+__device__ __forceinline__ const DirectProblemDev* direct_find(const DirectLaunch& dl, long long t) {
+    if (dl.many == nullptr) return &dl.single;
+    int lo = 0, hi = dl.nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (dl.many[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+    }
+    return &dl.many[lo];
+}
+
+struct TileCoord {
+    int n, i0, j0;
+};
+
+__device__ __forceinline__ TileCoord direct_tile(const DirectProblemDev* P, long long t) {
+    const long long lt = t - P->tile_base;
+    const long long per_img = static_cast<long long>(P->tiles_x) * P->tiles_y;
+    TileCoord c;
+    c.n = static_cast<int>(lt / per_img);
+    const int rem = static_cast<int>(lt % per_img);
+    c.i0 = (rem / P->tiles_x) * P->rows_n;
+    c.j0 = (rem % P->tiles_x) * P->J - P->e;
+    return c;
+}
+
+__device__ __forceinline__ bool epi_any_failed(bool failed) {
+    uint32_t any;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(any) : "r"(static_cast<uint32_t>(failed)) : "memory");
+    return any != 0;
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_constant__ DirectLaunch dl) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    int2* red = reinterpret_cast<int2*>(base + kStages * kStageBytes);
+    int2* run = red + kRedEntries;
+    DirectSmemTail* tail = reinterpret_cast<DirectSmemTail*>(run + kRunEntries);
+    volatile int* abort_flag = &tail->abort;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&tail->full[s]), 1);
+            mbar_init(smem_u32(&tail->empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tail->tfull[b]), 1);
+            mbar_init(smem_u32(&tail->tempty[b]), 4);
+        }
+        mbar_init(smem_u32(&tail->drain), 1);
+        tail->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&tail->tmem_base), kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tail->tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------ TMA producer
+        uint32_t it = 0;
+        bool ok = true;
+        for (long long t = blockIdx.x; ok && t < dl.total_tiles; t += gridDim.x) {
+            const DirectProblemDev* P = direct_find(dl, t);
+            if (dl.many != nullptr) {
+                tma_fence_acquire_desc(&P->tmA);
+                tma_fence_acquire_desc(&P->tmB);
+            }
+            const TileCoord tc = direct_tile(P, t);
+            const int* rb = P->meta;
+            const int* rows = P->meta + (P->n_pass + 1) + P->n_pass * 8;
+            const int xw = tc.j0 - (P->kw - 1) + P->ox;   // first image column of the K window (16-aligned)
+            for (int p = 0; ok && p < P->n_pass; ++p) {
+                for (int q = rb[p]; ok && q < rb[p + 1]; ++q) {
+                    const int r = rows[q];
+                    for (int kc = 0; kc < P->nk; ++kc) {
+                        const int s = static_cast<int>(it % kStages);
+                        const uint32_t ph = (it / kStages) & 1u;
+                        if (!mbar_wait(smem_u32(&tail->empty[s]), ph ^ 1u, abort_flag, dl.err)) { ok = false; break; }
+                        const uint32_t fb = smem_u32(&tail->full[s]);
+                        mbar_arrive_expect_tx(fb, kStageBytes);
+                        uint8_t* sa = base + s * kStageBytes;
+                        tma_load_2d(smem_u32(sa), &P->tmA, 0, (q * P->nk + kc) * 128, fb);
+                        tma_load_4d(smem_u32(sa + kStageA), &P->tmB, xw + 128 * kc, 0, tc.i0 - r + P->oy, tc.n, fb);
+                        ++it;
+                    }
+                }
+            }
+        }
+        if (!ok) {
+            // drain: let the copies already issued land before the CTA exits
+            const uint32_t nd = it < static_cast<uint32_t>(kStages) ? it : static_cast<uint32_t>(kStages);
+            for (uint32_t d = 0; d < nd; ++d) {
+                const uint32_t k = it - 1 - d;
+                mbar_wait_drain(smem_u32(&tail->full[k % kStages]), (k / kStages) & 1u);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // -------------------------------------------------------- MMA issuer
+        const uint32_t idesc = idesc_e4m3_f32(kDirectM, kDirectN);
+        uint32_t it = 0, unit = 0;
+        bool ok = true;
+        for (long long t = blockIdx.x; ok && t < dl.total_tiles; t += gridDim.x) {
+            const DirectProblemDev* P = direct_find(dl, t);
+            const int* rb = P->meta;
+            for (int p = 0; ok && p < P->n_pass; ++p) {
+                const uint32_t buf = unit & 1u;
+                if (!mbar_wait(smem_u32(&tail->tempty[buf]), ((unit >> 1) & 1u) ^ 1u, abort_flag, dl.err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + buf * kDirectN;
+                uint32_t acc = 0;
+                for (int q = rb[p]; ok && q < rb[p + 1]; ++q) {
+                    for (int kc = 0; kc < P->nk; ++kc) {
+                        const int s = static_cast<int>(it % kStages);
+                        const uint32_t ph = (it / kStages) & 1u;
+                        if (!mbar_wait(smem_u32(&tail->full[s]), ph, abort_flag, dl.err)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint8_t* sa = base + s * kStageBytes;
+                        const uint64_t adesc = umma_desc_sw128(smem_u32(sa));
+                        const uint64_t bdesc = umma_desc_sw128(smem_u32(sa + kStageA));
+                        const int nks = min(4, P->ksteps - 4 * kc);
+                        for (int ks = 0; ks < nks; ++ks) {
+                            // advance the start address by 32 B of K inside the 128-B swizzled rows
+                            tc_mma_f8(d_tmem, adesc + 2ull * ks, bdesc + 2ull * ks, idesc, acc);
+                            acc = 1;
+                        }
+                        tc_commit(smem_u32(&tail->empty[s]));
+                        ++it;
+                    }
+                }
+                if (ok) tc_commit(smem_u32(&tail->tfull[buf]));
+                ++unit;
+            }
+        }
+        if (!ok) {
+            tc_commit(smem_u32(&tail->drain));
+            mbar_wait_drain(smem_u32(&tail->drain), 0);
+        }
+    } else if (warp >= 2) {
+        // ----------------------------------------------------------- epilogue
+        const int quarter = warp & 3;                 // TMEM lane quarter this warp may access
+        const int m = quarter * 32 + lane;            // accumulator row = (group, column)
+        const int et = threadIdx.x - 64;              // 0..127
+        uint32_t unit = 0;
+        for (long long t = blockIdx.x; t < dl.total_tiles; t += gridDim.x) {
+            const DirectProblemDev* P = direct_find(dl, t);
+            const TileCoord tc = direct_tile(P, t);
+            const int J = P->J, G = P->G, rows_n = P->rows_n, Lpad = P->Lpad;
+            const int g = m / J;
+            const int* gw = P->meta + (P->n_pass + 1);
+            bool failed = false;
+            for (int p = 0; p < P->n_pass; ++p) {
+                const uint32_t buf = unit & 1u;
+                const bool ok = mbar_wait(smem_u32(&tail->tfull[buf]), (unit >> 1) & 1u, abort_flag, dl.err);
+                if (epi_any_failed(!ok)) { failed = true; break; }
+                tc_fence_after();
+                const int wg = (g < G) ? gw[p * 8 + g] : 0;
+                const uint32_t trow = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + buf * kDirectN;
+                for (int tr = 0; tr < rows_n; ++tr) {
+                    const uint32_t col0 = static_cast<uint32_t>(tr * Lpad);
+                    int top = -1;
+                    float cnt = 0.f;
+                    if (Lpad == 16) {
+                        float v[16];
+                        tmem_ld_32x32b_x16(trow + col0, v);
+                        tc_wait_ld();
+#pragma unroll
+                        for (int k = 0; k < 16; ++k)
+                            if (v[k] > 0.5f) { top = k; cnt = v[k]; }
+                    } else {
+                        for (int c = Lpad / 32 - 1; c >= 0; --c) {
+                            if (__all_sync(0xffffffffu, top >= 0)) break;
+                            float v[32];
+                            tmem_ld_32x32b_x32(trow + col0 + 32u * c, v);
+                            tc_wait_ld();
+                            if (top < 0) {
+#pragma unroll
+                                for (int k = 0; k < 32; ++k)
+                                    if (v[k] > 0.5f) { top = 32 * c + k; cnt = v[k]; }
+                            }
+                        }
+                    }
+                    red[tr * 128 + m] = (top >= 0) ? make_int2(top + wg, __float2int_rn(cnt)) : make_int2(-1, 0);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tail->tempty[buf]));
+                epi_bar();
+                const int pairs = rows_n * J;
+                for (int idx = et; idx < pairs; idx += 128) {
+                    const int tr = idx / J, jl = idx - tr * J;
+                    int best = -1, bc = 0;
+                    for (int gg = 0; gg < G; ++gg) {
+                        const int2 e = red[tr * 128 + gg * J + jl];
+                        if (e.x > best) { best = e.x; bc = e.y; }
+                        else if (e.x == best && e.x >= 0) bc += e.y;
+                    }
+                    int2 cur = make_int2(best, bc);
+                    if (p > 0) {
+                        const int2 prev = run[idx];
+                        if (prev.x > cur.x) cur = prev;
+                        else if (prev.x == cur.x && cur.x >= 0) cur.y += prev.y;
+                    }
+                    run[idx] = cur;
+                    if (p == P->n_pass - 1) {
+                        const int i = tc.i0 + tr, j = tc.j0 + jl;
+                        if (i < P->h && j >= 0 && j < P->w) {
+                            const int dval = cur.x < 0 ? 0 : cur.x;
+                            const long long o = (static_cast<long long>(tc.n) * P->h + i) * P->w + j;
+                            P->out[o] = P->erode ? (P->L - 1 - dval) : dval;
+                            if (P->out_cnt) P->out_cnt[o] = cur.x < 0 ? 0 : cur.y;
+                        }
+                    }
+                }
+                epi_bar();
+                ++unit;
+            }
+            if (failed) break;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------- Toeplitz
+// blocks[(q * nk + kc)][m][k] = 1.0 (E4M3) iff the tap (r_q, c) with
+// c = j + (kw - 1) - (128 kc + k), j = m mod J, lies in B and its offset is
+// the level of group g = m / J of the pass that owns row index q.
+__global__ void k_build_toeplitz(uint8_t* __restrict__ blocks, long long nbytes, const uint8_t* __restrict__ mask,
+                                 const int* __restrict__ off, const int* __restrict__ meta, int n_pass, int nk, int J,
+                                 int G, int kw) {
+    const int* rb = meta;
+    const int* gw = meta + (n_pass + 1);
+    const int* rows = gw + n_pass * 8;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nbytes;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = static_cast<int>(idx & 127);
+        const int m = static_cast<int>((idx >> 7) & 127);
+        const long long blk = idx >> 14;
+        const int q = static_cast<int>(blk / nk);
+        const int kc = static_cast<int>(blk % nk);
+        int p = 0;
+        while (p + 1 < n_pass && rb[p + 1] <= q) ++p;
+        const int r = rows[q];
+        const int g = m / J, j = m % J;
+        const int c = j + (kw - 1) - (128 * kc + k);
+        uint8_t v = 0;
+        if (g < G && c >= 0 && c < kw) {
+            const int t = r * kw + c;
+            if (mask[t] && off[t] == gw[p * 8 + g]) v = 0x38;
+        }
+        blocks[idx] = v;
+    }
+}
+
+DirectPlan::~DirectPlan() {
+    if (d_toeplitz) cudaFree(d_toeplitz);
+    if (d_meta) cudaFree(d_meta);
+}
+
+int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, DirectPlan* p) {
+    const int kh = se->kh, kw = se->kw;
+    p->L = f->L;
+    p->Lpad = 16;
+    while (p->Lpad < f->L) p->Lpad <<= 1;
+    p->rows_n = kDirectN / p->Lpad;
+    p->kh = kh;
+    p->kw = kw;
+    p->oy = se->oy;
+    p->ox = se->ox;
+    p->erode = erode;
+    p->h = f->h;
+    p->w = f->w;
+    p->nimg = f->n;
+    p->w_pad = (f->w + 15) & ~15;
+    // distinct offset levels among the taps
+    std::vector<int> levels;
+    int taps = 0, maxb = 0;
+    for (int t = 0; t < kh * kw; ++t) {
+        if (!se->mask[t]) continue;
+        ++taps;
+        maxb = std::max(maxb, static_cast<int>(se->offset[t]));
+        levels.push_back(se->offset[t]);
+    }
+    std::sort(levels.begin(), levels.end());
+    levels.erase(std::unique(levels.begin(), levels.end()), levels.end());
+    p->taps = taps;
+    p->maxb = maxb;
+    p->n_levels = static_cast<int>(levels.size());
+    if (taps == 0) return MORPH_OK;
+    // groups per pass: minimise passes x G x K-steps (the MMA work per output pixel)
+    long long best = -1;
+    for (int G = 1; G <= 8; G <<= 1) {
+        const int J = 128 / G;
+        const int ks = (J + kw - 1 + 31) / 32;
+        const int passes = (p->n_levels + G - 1) / G;
+        if (passes > kDirectMaxPasses) continue;
+        const long long cost = static_cast<long long>(passes) * G * ks;
+        // ties go to larger G: fewer passes re-read the image planes fewer times
+        if (best < 0 || cost <= best) {
+            best = cost;
+            p->G = G;
+        }
+    }
+    if (best < 0) return MORPH_E_UNSUPPORTED;
+    p->J = 128 / p->G;
+    p->ksteps = (p->J + kw - 1 + 31) / 32;
+    p->nk = (p->J + kw - 1 + 127) / 128;
+    p->n_pass = (p->n_levels + p->G - 1) / p->G;
+    const int a = (((kw - 1 - se->ox) % 16) + 16) % 16;
+    p->e = (16 - a) % 16;
+    p->tiles_x = (f->w + p->e + p->J - 1) / p->J;
+    p->tiles_y = (f->h + p->rows_n - 1) / p->rows_n;
+    p->tiles = static_cast<long long>(f->n) * p->tiles_x * p->tiles_y;
+    // meta: pass_row_begin[n_pass + 1], group_w[n_pass * 8], rows[]
+    std::vector<int> rb(p->n_pass + 1, 0), gw(p->n_pass * 8, 0), rows;
+    for (int ps = 0; ps < p->n_pass; ++ps) {
+        rb[ps] = static_cast<int>(rows.size());
+        for (int g = 0; g < p->G; ++g) {
+            const int li = ps * p->G + g;
+            gw[ps * 8 + g] = li < p->n_levels ? levels[li] : -1;
+        }
+        for (int r = 0; r < kh; ++r) {
+            bool any = false;
+            for (int c = 0; c < kw && !any; ++c) {
+                const int t = r * kw + c;
+                if (!se->mask[t]) continue;
+                for (int g = 0; g < p->G; ++g)
+                    if (gw[ps * 8 + g] == se->offset[t]) { any = true; break; }
+            }
+            if (any) rows.push_back(r);
+        }
+        if (static_cast<int>(rows.size()) == rb[ps]) return MORPH_E_UNSUPPORTED;   // every pass owns a tap
+    }
+    rb[p->n_pass] = static_cast<int>(rows.size());
+    p->active_rows_total = static_cast<long long>(rows.size());
+    p->meta.clear();
+    p->meta.insert(p->meta.end(), rb.begin(), rb.end());
+    p->meta.insert(p->meta.end(), gw.begin(), gw.end());
+    p->meta.insert(p->meta.end(), rows.begin(), rows.end());
+    p->toeplitz_blocks = p->active_rows_total * p->nk;
+    p->issued_flop = static_cast<double>(p->tiles) * static_cast<double>(p->active_rows_total) * p->ksteps * 2.0 *
+                     kDirectM * kDirectN * 32.0;
+
+    // device copies and the Toeplitz blocks
+    const size_t tb = static_cast<size_t>(p->toeplitz_blocks) * 128 * 128;
+    MORPH_CUDA_TRY(cudaMalloc(&p->d_toeplitz, tb));
+    MORPH_CUDA_TRY(cudaMalloc(&p->d_meta, p->meta.size() * sizeof(int)));
+    MORPH_CUDA_TRY(cudaMemcpy(p->d_meta, p->meta.data(), p->meta.size() * sizeof(int), cudaMemcpyHostToDevice));
+    uint8_t* d_mask = nullptr;
+    int* d_off = nullptr;
+    MORPH_CUDA_TRY(cudaMalloc(&d_mask, kh * kw));
+    MORPH_CUDA_TRY(cudaMalloc(&d_off, kh * kw * sizeof(int)));
+    std::vector<int> offv(kh * kw);
+    std::vector<uint8_t> maskv(kh * kw);
+    for (int t = 0; t < kh * kw; ++t) {
+        maskv[t] = se->mask[t] ? 1 : 0;
+        offv[t] = se->offset[t];
+    }
+    MORPH_CUDA_TRY(cudaMemcpy(d_mask, maskv.data(), kh * kw, cudaMemcpyHostToDevice));
+    MORPH_CUDA_TRY(cudaMemcpy(d_off, offv.data(), kh * kw * sizeof(int), cudaMemcpyHostToDevice));
+    {
+        long long blocks = (static_cast<long long>(tb) + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        k_build_toeplitz<<<static_cast<unsigned>(blocks), 256>>>(p->d_toeplitz, static_cast<long long>(tb), d_mask,
+                                                                d_off, p->d_meta, p->n_pass, p->nk, p->J, p->G, kw);
+        ctx->launches += 1;
+        MORPH_CUDA_TRY(cudaGetLastError());
+        MORPH_CUDA_TRY(cudaDeviceSynchronize());
+    }
+    cudaFree(d_mask);
+    cudaFree(d_off);
+    // tensor map of the Toeplitz blocks: rows of 128 B, boxes of 128 rows
+    const uint64_t dims[2] = {128, static_cast<uint64_t>(p->toeplitz_blocks) * 128};
+    const uint64_t strides[1] = {128};
+    const uint32_t box[2] = {128, 128};
+    return encode_tmap(&p->tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, p->d_toeplitz, dims, strides, box,
+                       CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,
+                         int32_t* out_cnt, long long tile_base, int* status) {
+    std::memset(static_cast<void*>(d), 0, sizeof(*d));
+    d->tmA = p.tmA;
+    const uint64_t dims[4] = {static_cast<uint64_t>(p.w), static_cast<uint64_t>(p.L), static_cast<uint64_t>(p.h),
+                              static_cast<uint64_t>(p.nimg)};
+    const uint64_t strides[3] = {static_cast<uint64_t>(p.w_pad), static_cast<uint64_t>(p.w_pad) * p.L,
+                                 static_cast<uint64_t>(p.w_pad) * p.L * p.h};
+    const uint32_t box[4] = {128, static_cast<uint32_t>(p.Lpad), static_cast<uint32_t>(p.rows_n), 1};
+    *status = encode_tmap(&d->tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<uint8_t*>(planes), dims, strides, box,
+                          CU_TENSOR_MAP_SWIZZLE_128B);
+    d->out = out;
+    d->out_cnt = out_cnt;
+    d->meta = p.d_meta;
+    d->h = p.h;
+    d->w = p.w;
+    d->nimg = p.nimg;
+    d->L = p.L;
+    d->Lpad = p.Lpad;
+    d->rows_n = p.rows_n;
+    d->J = p.J;
+    d->G = p.G;
+    d->n_pass = p.n_pass;
+    d->nk = p.nk;
+    d->ksteps = p.ksteps;
+    d->kw = p.kw;
+    d->oy = p.oy;
+    d->ox = p.ox;
+    d->e = p.e;
+    d->erode = p.erode;
+    d->tiles_x = p.tiles_x;
+    d->tiles_y = p.tiles_y;
+    d->tile_base = tile_base;
+    d->tiles = p.tiles;
+}
+
+int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st) {
+    if (dl.total_tiles <= 0) return MORPH_OK;
+    static int configured_device = -1;
+    const int smem = direct_smem_bytes(kStages);
+    if (configured_device != ctx->device) {
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        configured_device = ctx->device;
+    }
+    long long grid = dl.total_tiles < ctx->num_sms ? dl.total_tiles : ctx->num_sms;
+    k_direct_fp8<<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
+    ctx->launches += 1;
+    MORPH_CUDA_TRY(cudaGetLastError());
+    return MORPH_OK;
+}
+
+}  // namespace morph

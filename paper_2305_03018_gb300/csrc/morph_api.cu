@@ -1,0 +1,340 @@
+// C ABI of the library: context, argument validation (the S0 step: check
+// 0 <= b, 2 <= L, shapes), planning and dispatch to the kernels.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "morph_internal.h"
+#include "ptx.cuh"
+
+namespace morph {
+
+static thread_local char g_last_error[512] = {0};
+
+void set_last_cuda_error(cudaError_t e, const char* expr, const char* file, int line) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", expr, cudaGetErrorString(e), file, line);
+}
+
+// ------------------------------------------------------------ tensor maps
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode_fn() {
+    static PFN_encodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled>(p);
+    });
+    return fn;
+}
+
+int encode_tmap(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, const uint64_t* dims,
+                const uint64_t* strides_bytes, const uint32_t* box, CUtensorMapSwizzle swz) {
+    PFN_encodeTiled fn = get_encode_fn();
+    if (!fn) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled entry point not found");
+        return MORPH_E_CUDA;
+    }
+    cuuint64_t gd[5];
+    cuuint64_t gs[4];
+    cuuint32_t bx[5], es[5];
+    for (int i = 0; i < rank; ++i) {
+        gd[i] = dims[i];
+        bx[i] = box[i];
+        es[i] = 1;
+        if (i + 1 < rank) gs[i] = strides_bytes[i];
+    }
+    CUresult r = fn(m, dt, static_cast<cuuint32_t>(rank), base, gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled failed (%d), rank %d", (int)r, rank);
+        return MORPH_E_CUDA;
+    }
+    return MORPH_OK;
+}
+
+int ctx_workspace(morph_ctx* ctx, size_t bytes, void** out) {
+    if (bytes <= ctx->ws_bytes) {
+        *out = ctx->ws;
+        return MORPH_OK;
+    }
+    // Growing: earlier calls on any stream may still read the old buffer.
+    MORPH_CUDA_TRY(cudaDeviceSynchronize());
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    const size_t want = (bytes + (size_t(1) << 20) - 1) & ~((size_t(1) << 20) - 1);
+    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return MORPH_E_NOMEM;
+    }
+    ctx->ws_bytes = want;
+    *out = ctx->ws;
+    return MORPH_OK;
+}
+
+// ------------------------------------------------------------------ plans
+enum Route { ROUTE_EMPTY = 0, ROUTE_DIRECT = 1 };
+
+struct Plan {
+    int route = ROUTE_EMPTY;
+    DirectPlan direct;
+};
+
+// SE after the erosion-by-duality reflection (Sec. 2.1): b_reflected(y) = b(-y),
+// i.e. the box is flipped in both axes and the origin moves to (kh-1-oy, kw-1-ox).
+struct EffSE {
+    std::vector<uint8_t> mask;
+    std::vector<int32_t> off;
+    morph_se se;
+};
+
+static void effective_se(const morph_se* b, int erode, EffSE* e) {
+    const int kh = b->kh, kw = b->kw;
+    e->mask.resize(kh * kw);
+    e->off.resize(kh * kw);
+    for (int r = 0; r < kh; ++r)
+        for (int c = 0; c < kw; ++c) {
+            const int src = erode ? (kh - 1 - r) * kw + (kw - 1 - c) : r * kw + c;
+            e->mask[r * kw + c] = b->mask[src] ? 1 : 0;
+            e->off[r * kw + c] = b->mask[src] ? b->offset[src] : 0;
+        }
+    e->se = *b;
+    e->se.mask = e->mask.data();
+    e->se.offset = e->off.data();
+    if (erode) {
+        e->se.oy = kh - 1 - b->oy;
+        e->se.ox = kw - 1 - b->ox;
+    }
+}
+
+static int inval(const char* why) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "invalid argument: %s", why);
+    return MORPH_E_INVAL;
+}
+
+static int validate(const morph_image* f, const morph_se* b) {
+    if (!f || !b) return inval("null image or SE");
+    if (!f->data) return inval("null image data");
+    if (f->dtype < MORPH_U8 || f->dtype > MORPH_I32) return inval("dtype");
+    if (f->n < 1 || f->h < 1 || f->w < 1) return inval("image shape");
+    if (f->L < 2 || f->L > 256) return inval("L outside [2, 256]");
+    if (f->row_stride < f->w) return inval("row_stride < w");
+    if (f->batch_stride < static_cast<int64_t>(f->h - 1) * f->row_stride + f->w) return inval("batch_stride");
+    if (b->kh < 1 || b->kw < 1 || b->kh > 63 || b->kw > 63) return inval("SE box outside 1..63");
+    if (!b->mask || !b->offset) return inval("null SE mask or offset");
+    if (b->oy < -4096 || b->oy > 4096 || b->ox < -4096 || b->ox > 4096) return inval("SE origin");
+    for (int t = 0; t < b->kh * b->kw; ++t)
+        if (b->mask[t] && (b->offset[t] < 0 || b->offset[t] > 65535)) return inval("SE offset outside [0, 65535]");
+    return MORPH_OK;
+}
+
+static std::string plan_key(const morph_image* f, const morph_se* se, int erode, int route) {
+    std::string k;
+    char head[160];
+    std::snprintf(head, sizeof(head), "r%d|e%d|L%d|n%d|h%d|w%d|k%dx%d|o%d,%d|", route, erode, f->L, f->n, f->h, f->w,
+                  se->kh, se->kw, se->oy, se->ox);
+    k = head;
+    k.append(reinterpret_cast<const char*>(se->mask), static_cast<size_t>(se->kh) * se->kw);
+    k.append(reinterpret_cast<const char*>(se->offset), static_cast<size_t>(se->kh) * se->kw * sizeof(int32_t));
+    return k;
+}
+
+static int get_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, int route,
+                    std::shared_ptr<Plan>* out) {
+    const std::string key = plan_key(f, se, erode, route);
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        *out = it->second;
+        return MORPH_OK;
+    }
+    auto p = std::make_shared<Plan>();
+    int taps = 0;
+    for (int t = 0; t < se->kh * se->kw; ++t) taps += se->mask[t] ? 1 : 0;
+    if (taps == 0) {
+        p->route = ROUTE_EMPTY;
+    } else {
+        p->route = ROUTE_DIRECT;
+        int rc = build_direct_plan(ctx, f, se, erode, &p->direct);
+        if (rc) return rc;
+    }
+    ctx->plans.emplace(key, p);
+    *out = p;
+    return MORPH_OK;
+}
+
+static size_t planes_bytes(const morph_image* f) {
+    const size_t w_pad = (static_cast<size_t>(f->w) + 15) & ~size_t(15);
+    return static_cast<size_t>(f->n) * f->h * f->L * w_pad;
+}
+
+static int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
+                   const morph_opts* opts, cudaStream_t st) {
+    if (!ctx) return inval("null context");
+    if (!out) return inval("null output");
+    int rc = validate(f, b);
+    if (rc) return rc;
+    const int method = opts ? opts->method : MORPH_AUTO;
+    if (method != MORPH_AUTO && method != MORPH_DIRECT_FP8) return MORPH_E_UNSUPPORTED;
+    EffSE e;
+    effective_se(b, erode, &e);
+    std::shared_ptr<Plan> plan;
+    rc = get_plan(ctx, f, &e.se, erode, ROUTE_DIRECT, &plan);
+    if (rc) return rc;
+    const long long npx = static_cast<long long>(f->n) * f->h * f->w;
+    if (plan->route == ROUTE_EMPTY) return launch_fill_empty(ctx, out, cnt, npx, erode ? f->L - 1 : 0, st);
+
+    const DirectPlan& dp = plan->direct;
+    void* ws = nullptr;
+    rc = ctx_workspace(ctx, planes_bytes(f), &ws);
+    if (rc) return rc;
+    uint8_t* planes = static_cast<uint8_t*>(ws);
+
+    EncodeJob job;
+    job.src = f->data;
+    job.dtype = f->dtype;
+    job.n = f->n;
+    job.h = f->h;
+    job.w = f->w;
+    job.row_stride = f->row_stride;
+    job.batch_stride = f->batch_stride;
+    job.L = f->L;
+    job.flip = erode;
+    job.planes = planes;
+    job.w_pad = dp.w_pad;
+    job.item_base = 0;
+    const long long items = static_cast<long long>(f->n) * f->h * (dp.w_pad / 16);
+    rc = launch_encode(ctx, &job, 1, items, nullptr, st);
+    if (rc) return rc;
+
+    DirectLaunch dl;
+    std::memset(static_cast<void*>(&dl), 0, sizeof(dl));
+    direct_fill_problem(dp, &dl.single, planes, out, cnt, 0, &rc);
+    if (rc) return rc;
+    dl.many = nullptr;
+    dl.nprob = 1;
+    dl.total_tiles = dp.tiles;
+    dl.err = ctx->d_err;
+    return launch_direct(ctx, dl, st);
+}
+
+}  // namespace morph
+
+using namespace morph;
+
+extern "C" {
+
+int morph_ctx_create(int device, morph_ctx** out) {
+    if (!out) return MORPH_E_INVAL;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return MORPH_E_CUDA;
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    if (major != 10 || minor != 3) return MORPH_E_UNSUPPORTED;   // built for sm_103a only
+    morph_ctx* c = new (std::nothrow) morph_ctx();
+    if (!c) return MORPH_E_NOMEM;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&c->d_err, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return MORPH_E_NOMEM;
+    }
+    *out = c;
+    return MORPH_OK;
+}
+
+int morph_ctx_destroy(morph_ctx* ctx) {
+    if (!ctx) return MORPH_E_INVAL;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    ctx->plans.clear();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return MORPH_OK;
+}
+
+int morph_dilate(morph_ctx* ctx, const morph_image* f, const morph_se* b, int32_t* out, int32_t* out_count,
+                 const morph_opts* opts, morph_stream_t stream) {
+    return run_one(ctx, f, b, 0, out, out_count, opts, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int morph_erode(morph_ctx* ctx, const morph_image* f, const morph_se* b, int32_t* out, int32_t* out_count,
+                const morph_opts* opts, morph_stream_t stream) {
+    return run_one(ctx, f, b, 1, out, out_count, opts, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, int op, const morph_opts* opts,
+                     morph_plan_info* out) {
+    if (!ctx) return inval("null context");
+    if (!out) return inval("null output");
+    int rc = validate(f, b);
+    if (rc) return rc;
+    const int method = opts ? opts->method : MORPH_AUTO;
+    if (method != MORPH_AUTO && method != MORPH_DIRECT_FP8) return MORPH_E_UNSUPPORTED;
+    EffSE e;
+    effective_se(b, op ? 1 : 0, &e);
+    std::shared_ptr<Plan> plan;
+    rc = get_plan(ctx, f, &e.se, op ? 1 : 0, ROUTE_DIRECT, &plan);
+    if (rc) return rc;
+    std::memset(out, 0, sizeof(*out));
+    const DirectPlan& d = plan->direct;
+    out->method = MORPH_DIRECT_FP8;
+    out->R = f->L + d.maxb;
+    out->taps = d.taps;
+    out->groups = d.G;
+    out->passes = d.n_pass;
+    out->tile_w = d.J;
+    out->tile_h = d.rows_n;
+    out->est_flop = d.issued_flop;
+    out->workspace_bytes = planes_bytes(f);
+    return MORPH_OK;
+}
+
+int morph_stream_check(morph_ctx* ctx, morph_stream_t stream) {
+    if (!ctx) return MORPH_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+        return MORPH_E_CUDA;
+    }
+    unsigned int h = 0;
+    MORPH_CUDA_TRY(cudaMemcpy(&h, ctx->d_err, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h) MORPH_CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(h)));
+    if (h & MORPH_DEVERR_TIMEOUT) return MORPH_E_TIMEOUT;
+    if (h & MORPH_DEVERR_RANGE) return MORPH_E_RANGE;
+    if (h & MORPH_DEVERR_CONFIG) return MORPH_E_UNSUPPORTED;
+    return MORPH_OK;
+}
+
+const char* morph_strerror(int s) {
+    switch (s) {
+        case MORPH_OK: return "ok";
+        case MORPH_E_INVAL: return g_last_error[0] ? g_last_error : "invalid argument";
+        case MORPH_E_RANGE: return "pixel value outside [0, L)";
+        case MORPH_E_NOMEM: return "out of memory";
+        case MORPH_E_PRECISION: return "FP32 FFT round-off bound fails for this problem";
+        case MORPH_E_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+        case MORPH_E_TIMEOUT: return "a bounded device wait timed out";
+        case MORPH_E_UNSUPPORTED: return "unsupported request";
+        default: return "unknown status";
+    }
+}
+
+uint64_t morph_launch_count(const morph_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "morph.h"
+
+namespace morph {
+
+// ----------------------------------------------------------------- errors
+#define MORPH_CUDA_TRY(expr)                                   \
+    do {                                                       \
+        cudaError_t e__ = (expr);                              \
+        if (e__ != cudaSuccess) {                              \
+            morph::set_last_cuda_error(e__, #expr, __FILE__, __LINE__); \
+            return MORPH_E_CUDA;                               \
+        }                                                      \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* expr, const char* file, int line);
+
+// --------------------------------------------------- encoder (Step 1, Eq. 7)
+// One image batch is written as FP8 E4M3 indicator planes
+//   planes[n][i][v][j] = 1.0 if level(f(n,i,j)) == v else 0,  j < W,
+// with level(f) = f (dilation) or L-1-f (erosion by duality); row pitch
+// w_pad (a multiple of 16 bytes), columns w..w_pad-1 zero.
+struct EncodeJob {
+    const void* src;
+    int dtype;              // morph_dtype
+    int n, h, w;
+    long long row_stride, batch_stride;
+    int L;
+    int flip;               // 1: level = L-1-f
+    uint8_t* planes;
+    int w_pad;
+    long long item_base;    // first work item of this job (batched launch)
+};
+
+// ------------------------------------------- FP8 tcgen05 direct route (Step 2)
+constexpr int kDirectMaxPasses = 32;
+constexpr int kDirectN = 256;        // MMA N: image rows x padded levels per tile
+constexpr int kDirectM = 128;        // MMA M: offset groups x output columns
+
+struct DirectProblemDev {
+    CUtensorMap tmA;        // Toeplitz blocks: [blocks * 128 rows][128 B]
+    CUtensorMap tmB;        // planes: dims (w, L, h, n), box (128, Lpad, rows_n, 1)
+    int32_t* out;           // [n][h][w]
+    int32_t* out_cnt;       // nullable
+    const int* meta;        // pass_row_begin[n_pass+1], group_w[n_pass*8], rows[...]
+    int h, w, nimg, L;
+    int Lpad, rows_n, J, G;
+    int n_pass, nk, ksteps, kw;
+    int oy, ox, e, erode;
+    int tiles_x, tiles_y;
+    long long tile_base;    // first global tile of this problem
+    long long tiles;        // tiles of this problem
+};
+
+struct DirectLaunch {
+    DirectProblemDev single;         // used when many == nullptr
+    const DirectProblemDev* many;    // device array (batched launch)
+    int nprob;
+    long long total_tiles;
+    unsigned int* err;
+};
+
+struct DirectPlan {
+    int L = 0, Lpad = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0;
+    int kh = 0, kw = 0, oy = 0, ox = 0, e = 0, erode = 0;
+    int h = 0, w = 0, nimg = 0, w_pad = 0;
+    int tiles_x = 0, tiles_y = 0;
+    long long tiles = 0;
+    int n_levels = 0, taps = 0, maxb = 0;
+    long long active_rows_total = 0;  // sum over passes of active SE rows
+    std::vector<int> meta;
+    uint8_t* d_toeplitz = nullptr;
+    int* d_meta = nullptr;
+    long long toeplitz_blocks = 0;
+    CUtensorMap tmA;
+    double issued_flop = 0;           // dense MMA FLOP per launch
+    ~DirectPlan();
+};
+
+// ------------------------------------------------------------------- context
+struct Plan;
+
+}  // namespace morph
+
+struct morph_ctx {
+    int device = 0;
+    int num_sms = 0;
+    unsigned int* d_err = nullptr;        // device error word
+    void* ws = nullptr;                   // device workspace
+    size_t ws_bytes = 0;
+    uint64_t launches = 0;
+    std::unordered_map<std::string, std::shared_ptr<morph::Plan>> plans;
+};
+
+namespace morph {
+
+// Workspace of at least `bytes` (grows with a device synchronize).
+int ctx_workspace(morph_ctx* ctx, size_t bytes, void** out);
+
+// Encoding of tensor maps through the driver entry point.
+int encode_tmap(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, const uint64_t* dims,
+                const uint64_t* strides_bytes, const uint32_t* box, CUtensorMapSwizzle swz);
+
+// Kernel launchers (defined next to their kernels).
+int launch_encode(morph_ctx* ctx, const EncodeJob* jobs, int njobs, long long total_items,
+                  EncodeJob* d_jobs, cudaStream_t st);
+int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, DirectPlan* p);
+int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st);
+int direct_smem_bytes(int stages);
+int direct_stages();
+void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,
+                         int32_t* out_cnt, long long tile_base, int* status);
+int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st);
+
+}  // namespace morph

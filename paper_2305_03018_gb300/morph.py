@@ -1,0 +1,318 @@
+"""ctypes binding of the C ABI in ``include/morph.h`` (argument marshalling only).
+
+Every function named ``morph_*`` here calls the C entry point of the same
+name.  The small :class:`Context` helper turns torch tensors into the C
+structs (device pointers, strides, the current CUDA stream) and allocates
+the outputs with torch; every step of the computation runs in the library's
+CUDA kernels.  There is no CPU fallback: if the library is missing, loading
+fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libmorph_gb300.so")
+
+MORPH_OK, MORPH_E_INVAL, MORPH_E_RANGE, MORPH_E_NOMEM, MORPH_E_PRECISION, MORPH_E_CUDA, MORPH_E_TIMEOUT, \
+    MORPH_E_UNSUPPORTED = range(8)
+MORPH_U8, MORPH_U16, MORPH_I32 = 0, 1, 2
+MORPH_AUTO, MORPH_DIRECT_FP8, MORPH_FFT_F32, MORPH_FFT_F64 = 0, 1, 2, 3
+MORPH_F_ALLOW_UNPROVEN_F32, MORPH_F_VALIDATE = 1, 2
+METHODS = {"auto": MORPH_AUTO, "direct_fp8": MORPH_DIRECT_FP8, "fft_f32": MORPH_FFT_F32, "fft_f64": MORPH_FFT_F64}
+
+
+class morph_image(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int), ("n", ctypes.c_int), ("h", ctypes.c_int),
+                ("w", ctypes.c_int), ("row_stride", ctypes.c_int64), ("batch_stride", ctypes.c_int64),
+                ("L", ctypes.c_int)]
+
+
+class morph_se(ctypes.Structure):
+    _fields_ = [("kh", ctypes.c_int), ("kw", ctypes.c_int), ("oy", ctypes.c_int), ("ox", ctypes.c_int),
+                ("mask", ctypes.POINTER(ctypes.c_uint8)), ("offset", ctypes.POINTER(ctypes.c_int32))]
+
+
+class morph_opts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("flags", ctypes.c_int), ("count_err", ctypes.c_void_p)]
+
+
+class morph_plan_info(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("R", ctypes.c_int), ("taps", ctypes.c_int),
+                ("f32_bound", ctypes.c_double), ("f64_bound", ctypes.c_double),
+                ("fft_nx", ctypes.c_int), ("fft_ny", ctypes.c_int), ("groups", ctypes.c_int),
+                ("passes", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
+                ("est_flop", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class morph_problem(ctypes.Structure):
+    _fields_ = [("f", morph_image), ("se", morph_se), ("op", ctypes.c_int), ("out", ctypes.c_void_p),
+                ("out_count", ctypes.c_void_p)]
+
+
+# Every entry point include/morph.h declares, with its C signature.
+_P = ctypes.c_void_p
+_SIGS = {
+    "morph_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "morph_ctx_destroy": (ctypes.c_int, [_P]),
+    "morph_plan_query": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), ctypes.c_int,
+                                        ctypes.POINTER(morph_opts), ctypes.POINTER(morph_plan_info)]),
+    "morph_dilate": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P, _P,
+                                    ctypes.POINTER(morph_opts), _P]),
+    "morph_erode": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P, _P,
+                                   ctypes.POINTER(morph_opts), _P]),
+    "morph_dilate_backward": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P, _P, _P,
+                                             _P, _P, _P]),
+    "morph_run_batch": (ctypes.c_int, [_P, ctypes.POINTER(morph_problem), ctypes.c_int, ctypes.POINTER(morph_opts),
+                                       _P]),
+    "morph_batch_capture": (ctypes.c_int, [_P, ctypes.POINTER(morph_problem), ctypes.c_int,
+                                           ctypes.POINTER(morph_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "morph_batch_launch": (ctypes.c_int, [_P, _P]),
+    "morph_batch_destroy": (ctypes.c_int, [_P]),
+    "morph_stream_check": (ctypes.c_int, [_P, _P]),
+    "morph_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "morph_launch_count": (ctypes.c_uint64, [_P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+class MorphError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load_library().morph_strerror(status)
+        super().__init__(f"{where}: status {status} ({msg.decode() if msg else '?'})")
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status != MORPH_OK:
+        raise MorphError(status, where)
+
+
+# ------------------------------------------------- C entry points, same names
+def morph_ctx_create(device: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    check(load_library().morph_ctx_create(int(device), ctypes.byref(h)), "morph_ctx_create")
+    return h
+
+
+def morph_ctx_destroy(ctx) -> int:
+    return load_library().morph_ctx_destroy(ctx)
+
+
+def morph_plan_query(ctx, image, se, op, opts=None):
+    info = morph_plan_info()
+    check(load_library().morph_plan_query(ctx, ctypes.byref(image), ctypes.byref(se), int(op),
+                                          ctypes.byref(opts) if opts is not None else None, ctypes.byref(info)),
+          "morph_plan_query")
+    return info
+
+
+def morph_dilate(ctx, image, se, out_ptr, cnt_ptr, opts, stream) -> int:
+    return load_library().morph_dilate(ctx, ctypes.byref(image), ctypes.byref(se), out_ptr, cnt_ptr,
+                                       ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def morph_erode(ctx, image, se, out_ptr, cnt_ptr, opts, stream) -> int:
+    return load_library().morph_erode(ctx, ctypes.byref(image), ctypes.byref(se), out_ptr, cnt_ptr,
+                                      ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def morph_dilate_backward(ctx, image, se, d_ptr, cd_ptr, g_ptr, gin_ptr, gse_ptr, stream) -> int:
+    return load_library().morph_dilate_backward(ctx, ctypes.byref(image), ctypes.byref(se), d_ptr, cd_ptr, g_ptr,
+                                                gin_ptr, gse_ptr, stream)
+
+
+def morph_run_batch(ctx, problems, opts, stream) -> int:
+    arr = (morph_problem * len(problems))(*problems)
+    return load_library().morph_run_batch(ctx, arr, len(problems), ctypes.byref(opts) if opts is not None else None,
+                                          stream)
+
+
+def morph_batch_capture(ctx, problems, opts):
+    arr = (morph_problem * len(problems))(*problems)
+    h = ctypes.c_void_p()
+    check(load_library().morph_batch_capture(ctx, arr, len(problems),
+                                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(h)),
+          "morph_batch_capture")
+    return h
+
+
+def morph_batch_launch(batch, stream) -> int:
+    return load_library().morph_batch_launch(batch, stream)
+
+
+def morph_batch_destroy(batch) -> int:
+    return load_library().morph_batch_destroy(batch)
+
+
+def morph_stream_check(ctx, stream) -> int:
+    return load_library().morph_stream_check(ctx, stream)
+
+
+def morph_strerror(status: int) -> str:
+    r = load_library().morph_strerror(int(status))
+    return r.decode() if r else ""
+
+
+def morph_launch_count(ctx) -> int:
+    return int(load_library().morph_launch_count(ctx))
+
+
+# ------------------------------------------------------------ torch helpers
+_DT = {"uint8": MORPH_U8, "uint16": MORPH_U16, "int32": MORPH_I32}
+
+
+def make_image(t, L: int) -> morph_image:
+    """C view of a CUDA integer tensor of shape [N, H, W] (or [H, W])."""
+    import torch
+    if t.dim() == 2:
+        t = t.unsqueeze(0)
+    if t.dim() != 3 or not t.is_cuda:
+        raise ValueError("image must be a CUDA tensor [N, H, W] or [H, W]")
+    name = str(t.dtype).replace("torch.", "")
+    if name not in _DT:
+        raise ValueError(f"unsupported image dtype {t.dtype}")
+    if t.stride(2) != 1:
+        raise ValueError("image columns must be contiguous")
+    img = morph_image()
+    img.data = t.data_ptr()
+    img.dtype = _DT[name]
+    img.n, img.h, img.w = (int(s) for s in t.shape)
+    # a size-1 dimension may carry any stride (0 after a broadcasting view): use the packed one
+    img.row_stride = int(t.stride(1)) if img.h > 1 else img.w
+    img.batch_stride = int(t.stride(0)) if img.n > 1 else img.h * img.row_stride
+    img.L = int(L)
+    return img
+
+
+class SEView:
+    """Host arrays of an SE kept alive next to the C struct that points at them."""
+
+    def __init__(self, mask, offset, origin):
+        self.mask = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        self.offset = np.ascontiguousarray(np.asarray(offset), dtype=np.int32)
+        if self.mask.ndim != 2 or self.offset.shape != self.mask.shape:
+            raise ValueError("mask and offset must be 2-D arrays of one shape")
+        self.c = morph_se()
+        self.c.kh, self.c.kw = (int(s) for s in self.mask.shape)
+        self.c.oy, self.c.ox = int(origin[0]), int(origin[1])
+        self.c.mask = self.mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        self.c.offset = self.offset.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def se_view(se) -> SEView:
+    """Accepts a workloads.SE-like object (mask, offset, origin) or a tuple."""
+    if isinstance(se, SEView):
+        return se
+    if isinstance(se, tuple):
+        return SEView(*se)
+    return SEView(se.mask, se.offset, se.origin)
+
+
+def make_opts(method="auto", allow_unproven_f32=False, validate=False, count_err=None) -> morph_opts:
+    o = morph_opts()
+    o.method = METHODS[method] if isinstance(method, str) else int(method)
+    o.flags = (MORPH_F_ALLOW_UNPROVEN_F32 if allow_unproven_f32 else 0) | (MORPH_F_VALIDATE if validate else 0)
+    o.count_err = count_err.data_ptr() if count_err is not None else None
+    return o
+
+
+def current_stream_handle(device=None):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Context:
+    """One library context per CUDA device (not thread-safe)."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        torch.cuda.init()
+        self.device = int(device)
+        with torch.cuda.device(self.device):
+            self.handle = morph_ctx_create(self.device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            morph_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- forward -------------------------------------------------------------
+    def _run(self, op, f, L, se, method, count, stream, allow_unproven_f32=False, count_err=None, out=None,
+             out_count=None):
+        import torch
+        img = make_image(f, L)
+        sv = se_view(se)
+        shape = (img.n, img.h, img.w)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.int32, device=f.device)
+        if count and out_count is None:
+            out_count = torch.empty(shape, dtype=torch.int32, device=f.device)
+        opts = make_opts(method, allow_unproven_f32, count_err is not None, count_err)
+        st = stream if stream is not None else current_stream_handle(f.device)
+        fn = morph_dilate if op == 0 else morph_erode
+        check(fn(self.handle, img, sv.c, out.data_ptr(), out_count.data_ptr() if count else None, opts, st),
+              "morph_dilate" if op == 0 else "morph_erode")
+        return (out, out_count) if count else out
+
+    def dilate(self, f, L, se, method="auto", count=False, stream=None, **kw):
+        return self._run(0, f, L, se, method, count, stream, **kw)
+
+    def erode(self, f, L, se, method="auto", count=False, stream=None, **kw):
+        return self._run(1, f, L, se, method, count, stream, **kw)
+
+    def plan(self, f, L, se, op=0, method="auto", allow_unproven_f32=False):
+        img = make_image(f, L)
+        sv = se_view(se)
+        return morph_plan_query(self.handle, img, sv.c, op, make_opts(method, allow_unproven_f32))
+
+    def check(self, stream=None):
+        st = stream if stream is not None else current_stream_handle(self.device)
+        check(morph_stream_check(self.handle, st), "morph_stream_check")
+
+    def launches(self) -> int:
+        return morph_launch_count(self.handle)
+
+
+_contexts = {}
+
+
+def get_context(device: int = 0) -> Context:
+    with _lock:
+        c = _contexts.get(int(device))
+    if c is None:
+        c = Context(device)
+        with _lock:
+            _contexts[int(device)] = c
+    return c
