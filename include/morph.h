@@ -189,6 +189,24 @@ const char *morph_strerror(int status);
  * creation (every launch, every route). */
 uint64_t morph_launch_count(const morph_ctx *ctx);
 
+/* Per-kernel device time, summed over the launches recorded while profiling
+ * was on. */
+typedef struct {
+    char name[48];           /* kernel name */
+    uint64_t launches;
+    double total_ms;         /* sum of CUDA-event durations on the launching stream */
+} morph_kernel_time;
+
+/* on != 0: record a CUDA event pair on the launching stream around every
+ * kernel the context launches from now on (a timing hook; adds a few
+ * microseconds of host work per launch).  on == 0: stop recording. */
+int morph_profile_enable(morph_ctx *ctx, int on);
+
+/* Synchronize the device, turn the recorded event pairs into per-kernel
+ * totals, write up to `cap` of them to `out`, set *n to the number of
+ * kernels, and clear the record. */
+int morph_profile_read(morph_ctx *ctx, morph_kernel_time *out, int cap, int *n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -507,7 +507,9 @@ int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st) {
         configured_device = ctx->device;
     }
     long long grid = dl.total_tiles < ctx->num_sms ? dl.total_tiles : ctx->num_sms;
+    prof_begin(ctx, st, "k_direct_fp8");
     k_direct_fp8<<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
+    prof_end(ctx, st);
     ctx->launches += 1;
     MORPH_CUDA_TRY(cudaGetLastError());
     return MORPH_OK;

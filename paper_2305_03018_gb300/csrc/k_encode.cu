@@ -85,8 +85,10 @@ int launch_encode(morph_ctx* ctx, const EncodeJob* jobs, int njobs, long long to
     const long long cap = static_cast<long long>(ctx->num_sms) * 16;
     if (blocks > cap) blocks = cap;
     EncodeJob single = jobs[0];
+    prof_begin(ctx, st, "k_encode_planes");
     k_encode_planes<<<static_cast<unsigned>(blocks), threads, 0, st>>>(njobs > 1 ? d_jobs : nullptr, njobs, single,
                                                                       total_items, ctx->d_err);
+    prof_end(ctx, st);
     ctx->launches += 1;
     MORPH_CUDA_TRY(cudaGetLastError());
     return MORPH_OK;
@@ -105,7 +107,9 @@ int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, i
     if (n <= 0) return MORPH_OK;
     long long blocks = (n + 255) / 256;
     if (blocks > ctx->num_sms * 8LL) blocks = ctx->num_sms * 8LL;
+    prof_begin(ctx, st, "k_fill_empty");
     k_fill_empty<<<static_cast<unsigned>(blocks), 256, 0, st>>>(out, cnt, n, value);
+    prof_end(ctx, st);
     ctx->launches += 1;
     MORPH_CUDA_TRY(cudaGetLastError());
     return MORPH_OK;

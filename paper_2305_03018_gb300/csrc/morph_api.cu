@@ -60,6 +60,36 @@ int encode_tmap(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, co
     return MORPH_OK;
 }
 
+static cudaEvent_t prof_event(morph_ctx* ctx) {
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void prof_begin(morph_ctx* ctx, cudaStream_t st, const char* name) {
+    if (!ctx->prof_on) return;
+    morph_prof_rec r;
+    r.name = name;
+    r.a = prof_event(ctx);
+    r.b = prof_event(ctx);
+    if (!r.a || !r.b) return;
+    cudaEventRecord(r.a, st);
+    ctx->prof.push_back(r);
+}
+
+void prof_end(morph_ctx* ctx, cudaStream_t st) {
+    if (!ctx->prof_on || ctx->prof.empty()) return;
+    cudaEventRecord(ctx->prof.back().b, st);
+}
+
 int ctx_workspace(morph_ctx* ctx, size_t bytes, void** out) {
     if (bytes <= ctx->ws_bytes) {
         *out = ctx->ws;
@@ -262,6 +292,11 @@ int morph_ctx_destroy(morph_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     ctx->plans.clear();
+    for (auto& r : ctx->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;
@@ -336,5 +371,42 @@ const char* morph_strerror(int s) {
 }
 
 uint64_t morph_launch_count(const morph_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int morph_profile_enable(morph_ctx* ctx, int on) {
+    if (!ctx) return MORPH_E_INVAL;
+    ctx->prof_on = on != 0;
+    return MORPH_OK;
+}
+
+int morph_profile_read(morph_ctx* ctx, morph_kernel_time* out, int cap, int* n) {
+    if (!ctx || (cap > 0 && !out)) return MORPH_E_INVAL;
+    MORPH_CUDA_TRY(cudaDeviceSynchronize());
+    std::vector<morph_kernel_time> acc;
+    for (const morph_prof_rec& r : ctx->prof) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        morph_kernel_time* slot = nullptr;
+        for (auto& k : acc)
+            if (std::strncmp(k.name, r.name, sizeof(k.name)) == 0) slot = &k;
+        if (!slot) {
+            morph_kernel_time k;
+            std::memset(&k, 0, sizeof(k));
+            std::strncpy(k.name, r.name, sizeof(k.name) - 1);
+            acc.push_back(k);
+            slot = &acc.back();
+        }
+        slot->launches += 1;
+        slot->total_ms += ms;
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof.clear();
+    if (n) *n = static_cast<int>(acc.size());
+    for (int i = 0; i < cap && i < static_cast<int>(acc.size()); ++i) out[i] = acc[i];
+    return MORPH_OK;
+}
 
 }  // extern "C"

@@ -92,7 +92,15 @@ struct Plan;
 
 }  // namespace morph
 
+struct morph_prof_rec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+
 struct morph_ctx {
+    bool prof_on = false;
+    std::vector<morph_prof_rec> prof;     // recorded event pairs
+    std::vector<cudaEvent_t> prof_pool;   // free events
     int device = 0;
     int num_sms = 0;
     unsigned int* d_err = nullptr;        // device error word
@@ -103,6 +111,10 @@ struct morph_ctx {
 };
 
 namespace morph {
+
+// Timing hook: event pair around one launch while profiling is on.
+void prof_begin(morph_ctx* ctx, cudaStream_t st, const char* name);
+void prof_end(morph_ctx* ctx, cudaStream_t st);
 
 // Workspace of at least `bytes` (grows with a device synchronize).
 int ctx_workspace(morph_ctx* ctx, size_t bytes, void** out);

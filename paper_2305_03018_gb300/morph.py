@@ -55,6 +55,10 @@ class morph_problem(ctypes.Structure):
                 ("out_count", ctypes.c_void_p)]
 
 
+class morph_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
 # Every entry point include/morph.h declares, with its C signature.
 _P = ctypes.c_void_p
 _SIGS = {
@@ -77,6 +81,9 @@ _SIGS = {
     "morph_stream_check": (ctypes.c_int, [_P, _P]),
     "morph_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "morph_launch_count": (ctypes.c_uint64, [_P]),
+    "morph_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "morph_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(morph_kernel_time), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lock = threading.Lock()
@@ -181,6 +188,19 @@ def morph_strerror(status: int) -> str:
 
 def morph_launch_count(ctx) -> int:
     return int(load_library().morph_launch_count(ctx))
+
+
+def morph_profile_enable(ctx, on: bool) -> int:
+    return load_library().morph_profile_enable(ctx, 1 if on else 0)
+
+
+def morph_profile_read(ctx):
+    """Per-kernel totals {name: (launches, total_ms)} of the recorded launches."""
+    cap = 64
+    arr = (morph_kernel_time * cap)()
+    n = ctypes.c_int(0)
+    check(load_library().morph_profile_read(ctx, arr, cap, ctypes.byref(n)), "morph_profile_read")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, cap))}
 
 
 # ------------------------------------------------------------ torch helpers
@@ -303,6 +323,12 @@ class Context:
 
     def launches(self) -> int:
         return morph_launch_count(self.handle)
+
+    def profile(self, on: bool):
+        check(morph_profile_enable(self.handle, on), "morph_profile_enable")
+
+    def profile_read(self):
+        return morph_profile_read(self.handle)
 
 
 _contexts = {}
