@@ -207,6 +207,32 @@ int morph_profile_enable(morph_ctx *ctx, int on);
  * kernels, and clear the record. */
 int morph_profile_read(morph_ctx *ctx, morph_kernel_time *out, int cap, int *n);
 
+/* Dilation (op = 0) or erosion (op = 1) by the FP8 tensor-core route,
+ * without allocating any device memory and without a context.  The paper has
+ * no counterpart: this serves callers that cannot call cudaMalloc / cudaFree,
+ * such as code running where another component owns the device memory
+ * budget, or host paths that must not block on the device-wide
+ * synchronisation an allocation may imply.
+ *
+ * Inputs and outputs are as for morph_dilate / morph_erode (out and the
+ * nullable out_count are int32 [n][h][w] device buffers of the caller).
+ * dev_status: nullable device uint32; when given, it receives the device
+ * error bits of this call (0 = ok, 1 = a pixel outside [0, L), 2 = a bounded
+ * wait gave up), written in stream order after the result.
+ *
+ * Everything else (error word, plan metadata, SE Toeplitz blocks, FP8
+ * indicator planes) lives in one fixed 64 MiB __device__ array that every GPU
+ * loading the library holds until the process exits.  A problem fits when
+ * n*h*L*round_up(w, 16) bytes of planes plus the SE blocks (up to 2 MB) fit in
+ * 64 MiB; a larger one is rejected with MORPH_E_NOMEM before any work is
+ * queued.  The first call on a device (with that device current) looks up the
+ * array's device address once; make that first call before any stream
+ * capture.  All calls share the array: each call clears the error word it
+ * uses, and calls whose GPU work overlaps race with each other (issue them in
+ * one stream).  Plans are rebuilt on every call. */
+int morph_run_noalloc(const morph_image *f, const morph_se *b, int op, int32_t *out, int32_t *out_count,
+                      uint32_t *dev_status, morph_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

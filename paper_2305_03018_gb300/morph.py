@@ -81,6 +81,8 @@ _SIGS = {
     "morph_stream_check": (ctypes.c_int, [_P, _P]),
     "morph_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "morph_launch_count": (ctypes.c_uint64, [_P]),
+    "morph_run_noalloc": (ctypes.c_int, [ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), ctypes.c_int, _P, _P,
+                                         _P, _P]),
     "morph_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "morph_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(morph_kernel_time), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int)]),
@@ -188,6 +190,12 @@ def morph_strerror(status: int) -> str:
 
 def morph_launch_count(ctx) -> int:
     return int(load_library().morph_launch_count(ctx))
+
+
+def morph_run_noalloc(image, se, op, out_ptr, cnt_ptr, status_ptr, stream) -> int:
+    """Allocation-free dilation (op 0) / erosion (op 1); see include/morph.h."""
+    return load_library().morph_run_noalloc(ctypes.byref(image), ctypes.byref(se), int(op), out_ptr, cnt_ptr,
+                                            status_ptr, stream)
 
 
 def morph_profile_enable(ctx, on: bool) -> int:
