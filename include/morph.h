@@ -32,7 +32,8 @@
  *     found on the device (a pixel outside [0, L)) are reported by
  *     morph_stream_check().
  *   - A context is bound to one device and is not thread-safe: use one
- *     context per host thread.
+ *     context per host thread.  Calls through one context share its device
+ *     workspace: issue them on one stream (or order the streams).
  */
 #ifndef MORPH_H
 #define MORPH_H

@@ -292,6 +292,7 @@ int morph_ctx_destroy(morph_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     ctx->plans.clear();
+    ctx->aux_plans.clear();
     for (auto& r : ctx->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

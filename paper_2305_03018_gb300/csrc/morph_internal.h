@@ -108,6 +108,7 @@ struct morph_ctx {
     size_t ws_bytes = 0;
     uint64_t launches = 0;
     std::unordered_map<std::string, std::shared_ptr<morph::Plan>> plans;
+    std::unordered_map<std::string, std::shared_ptr<void>> aux_plans;   // backward tap lists, ...
 };
 
 namespace morph {

@@ -2,8 +2,6 @@
 #include "morph_internal.h"
 
 extern "C" {
-int morph_dilate_backward(morph_ctx*, const morph_image*, const morph_se*, const int32_t*, const int32_t*,
-                          const float*, float*, float*, morph_stream_t) { return MORPH_E_UNSUPPORTED; }
 int morph_run_batch(morph_ctx*, const morph_problem*, int, const morph_opts*, morph_stream_t) {
     return MORPH_E_UNSUPPORTED;
 }

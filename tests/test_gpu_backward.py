@@ -1,0 +1,76 @@
+"""GPU backward (tie-split argmax gradient) against the fp64 CPU oracle.
+
+Tolerance from the arithmetic: the library sums fp32 terms g(x)/cD(x).
+grad_in(p) adds at most |B| terms in sequence: |error| <= (|B| + 2) u S(p);
+grad_se(y) adds each 8192-pixel chunk with a depth of at most 32 + 5 + 8
+additions, then the chunks in fp64: |error| <= 48 u S(y) + u |grad_se(y)|,
+where u = 2^-24 and S is the same sum taken over |g| (the oracle with |g|).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_03018_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -24
+
+
+def _oracle_grads(f, L, mask, off, origin, g):
+    D, cD = oracle.dilate(f, L, mask, off, origin)
+    gf, gb = oracle.dilate_backward(f, L, mask, off, origin, D, cD, g)
+    sf, sb = oracle.dilate_backward(f, L, mask, off, origin, D, cD, np.abs(g))
+    return D, cD, gf, gb, sf, sb
+
+
+def _check(x_np, b_np, mask, origin, L, g_np):
+    from paper_2305_03018_gb300.autograd import dilate
+    x = torch.from_numpy(x_np).cuda().requires_grad_(True)
+    b = torch.from_numpy(b_np).cuda().requires_grad_(True)
+    y = dilate(x, b, L, mask, origin)
+    y.backward(torch.from_numpy(g_np).cuda())
+    torch.cuda.synchronize()
+    H, W = x_np.shape[-2:]
+    f = x_np.reshape(-1, H, W).astype(np.int32)
+    off = b_np.astype(np.int32)
+    D, cD, gf, gb, sf, sb = _oracle_grads(f, L, mask, off, origin, g_np.reshape(-1, H, W).astype(np.float64))
+    np.testing.assert_array_equal(y.detach().cpu().numpy().reshape(D.shape).astype(np.int64), D)
+    ntaps = int(np.count_nonzero(mask))
+    gx = x.grad.cpu().numpy().reshape(gf.shape).astype(np.float64)
+    assert (np.abs(gx - gf) <= (ntaps + 2) * U * sf + 1e-30).all(), np.abs(gx - gf).max()
+    gbg = b.grad.cpu().numpy().astype(np.float64)
+    assert (np.abs(gbg - gb) <= 48 * U * sb + U * np.abs(gb) + 1e-30).all(), np.abs(gbg - gb).max()
+    assert (gbg[np.asarray(mask) == 0] == 0).all()
+    return x.grad.clone(), b.grad.clone()
+
+
+def test_c4_layer_forward_backward():
+    c = wl.c4_layer()
+    mask = np.ones((9, 9), np.uint8)
+    gx1, gb1 = _check(c.x, c.b, mask, c.origin, c.L, c.g)
+    gx2, gb2 = _check(c.x, c.b, mask, c.origin, c.L, c.g)
+    assert torch.equal(gx1, gx2) and torch.equal(gb1, gb2)        # deterministic
+
+
+def test_irregular_se_with_ties():
+    g = wl.rng(31)
+    x = g.integers(0, 4, size=(3, 1, 37, 53)).astype(np.float32)       # L = 4: many ties
+    se = wl.se_random(g, 7, 5, 0.6, 2, origin=(1, 4))
+    up = g.standard_normal(x.shape).astype(np.float32)
+    _check(x, se.offset.astype(np.float32), se.mask, se.origin, 4, up)
+
+
+def test_single_point_se_closed_form():
+    g = wl.rng(32)
+    x = g.integers(0, 16, size=(2, 1, 20, 24)).astype(np.float32)
+    mask = np.zeros((3, 3), np.uint8)
+    mask[0, 2] = 1
+    off = np.zeros((3, 3), np.float32)
+    off[0, 2] = 5
+    up = g.standard_normal(x.shape).astype(np.float32)
+    gx, gb = _check(x, off, mask, (1, 1), 16, up)
+    # y = (-1, 1): p receives g(p + y) where p + y is inside
+    exp = np.zeros_like(up)
+    exp[:, :, 1:, :-1] = up[:, :, :-1, 1:]
+    np.testing.assert_allclose(gx.cpu().numpy(), exp, rtol=0, atol=0)
