@@ -112,11 +112,12 @@ int ctx_workspace(morph_ctx* ctx, size_t bytes, void** out) {
 }
 
 // ------------------------------------------------------------------ plans
-enum Route { ROUTE_EMPTY = 0, ROUTE_DIRECT = 1 };
+enum Route { ROUTE_EMPTY = 0, ROUTE_DIRECT = 1, ROUTE_FFT32 = 2, ROUTE_FFT64 = 3 };
 
 struct Plan {
     int route = ROUTE_EMPTY;
     DirectPlan direct;
+    FftPlan fft;
 };
 
 // SE after the erosion-by-duality reflection (Sec. 2.1): b_reflected(y) = b(-y),
@@ -167,11 +168,11 @@ static int validate(const morph_image* f, const morph_se* b) {
     return MORPH_OK;
 }
 
-static std::string plan_key(const morph_image* f, const morph_se* se, int erode, int route) {
+static std::string plan_key(const morph_image* f, const morph_se* se, int erode, int route, bool unproven = false) {
     std::string k;
     char head[160];
-    std::snprintf(head, sizeof(head), "r%d|e%d|L%d|n%d|h%d|w%d|k%dx%d|o%d,%d|", route, erode, f->L, f->n, f->h, f->w,
-                  se->kh, se->kw, se->oy, se->ox);
+    std::snprintf(head, sizeof(head), "r%d%s|e%d|L%d|n%d|h%d|w%d|k%dx%d|o%d,%d|", route, unproven ? "u" : "", erode,
+                  f->L, f->n, f->h, f->w, se->kh, se->kw, se->oy, se->ox);
     k = head;
     k.append(reinterpret_cast<const char*>(se->mask), static_cast<size_t>(se->kh) * se->kw);
     k.append(reinterpret_cast<const char*>(se->offset), static_cast<size_t>(se->kh) * se->kw * sizeof(int32_t));
@@ -179,8 +180,8 @@ static std::string plan_key(const morph_image* f, const morph_se* se, int erode,
 }
 
 static int get_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, int route,
-                    std::shared_ptr<Plan>* out) {
-    const std::string key = plan_key(f, se, erode, route);
+                    std::shared_ptr<Plan>* out, bool unproven = false) {
+    const std::string key = plan_key(f, se, erode, route, unproven);
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
         *out = it->second;
@@ -191,9 +192,13 @@ static int get_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, in
     for (int t = 0; t < se->kh * se->kw; ++t) taps += se->mask[t] ? 1 : 0;
     if (taps == 0) {
         p->route = ROUTE_EMPTY;
-    } else {
+    } else if (route == ROUTE_DIRECT) {
         p->route = ROUTE_DIRECT;
         int rc = build_direct_plan(ctx, f, se, erode, &p->direct);
+        if (rc) return rc;
+    } else {
+        p->route = route;
+        int rc = build_fft_plan(ctx, f, se, route == ROUTE_FFT32 ? 4 : 8, unproven, &p->fft);
         if (rc) return rc;
     }
     ctx->plans.emplace(key, p);
@@ -206,6 +211,37 @@ static size_t planes_bytes(const morph_image* f) {
     return static_cast<size_t>(f->n) * f->h * f->L * w_pad;
 }
 
+// Route for a request.  AUTO compares a time estimate of the FP8 direct route
+// (issued dense FLOP at the tensor rate the kernel reaches) with the FP32 FFT
+// route when that route's a-priori bound proves it exact; FP64 is never
+// chosen automatically (it is exact but slow on this part).
+static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, int method,
+                        bool unproven, int* route) {
+    if (method == MORPH_DIRECT_FP8) { *route = ROUTE_DIRECT; return MORPH_OK; }
+    if (method == MORPH_FFT_F64) { *route = ROUTE_FFT64; return MORPH_OK; }
+    if (method == MORPH_FFT_F32) { *route = ROUTE_FFT32; return MORPH_OK; }
+    if (method != MORPH_AUTO) return MORPH_E_INVAL;
+    const std::string key = "auto|" + plan_key(f, se, erode, 0);
+    auto it = ctx->route_cache.find(key);
+    if (it != ctx->route_cache.end()) { *route = it->second; return MORPH_OK; }
+    std::shared_ptr<Plan> dp;
+    int rc = get_plan(ctx, f, se, erode, ROUTE_DIRECT, &dp);
+    if (rc) return rc;
+    *route = ROUTE_DIRECT;
+    if (dp->route == ROUTE_DIRECT) {
+        const double t_direct = dp->direct.issued_flop / 2.0e15;
+        FftPlan fp;
+        if (plan_fft_tiles(f, se, 4, false, &fp) == MORPH_OK) {
+            const double bytes = 5.0 * fp.K * static_cast<double>(fp.ax.N) * fp.ay.N * 8.0 * fp.ntiles;
+            const double t_fft = fp.flop / 2.5e13 + bytes / 4.0e12;
+            if (t_fft < t_direct) *route = ROUTE_FFT32;
+        }
+    }
+    (void)unproven;
+    ctx->route_cache.emplace(key, *route);
+    return MORPH_OK;
+}
+
 static int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
                    const morph_opts* opts, cudaStream_t st) {
     if (!ctx) return inval("null context");
@@ -213,14 +249,20 @@ static int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int 
     int rc = validate(f, b);
     if (rc) return rc;
     const int method = opts ? opts->method : MORPH_AUTO;
-    if (method != MORPH_AUTO && method != MORPH_DIRECT_FP8) return MORPH_E_UNSUPPORTED;
+    const bool unproven = opts && (opts->flags & MORPH_F_ALLOW_UNPROVEN_F32);
     EffSE e;
     effective_se(b, erode, &e);
+    int route = ROUTE_DIRECT;
+    rc = choose_route(ctx, f, &e.se, erode, method, unproven, &route);
+    if (rc) return rc;
     std::shared_ptr<Plan> plan;
-    rc = get_plan(ctx, f, &e.se, erode, ROUTE_DIRECT, &plan);
+    rc = get_plan(ctx, f, &e.se, erode, route, &plan, route == ROUTE_FFT32 && unproven);
     if (rc) return rc;
     const long long npx = static_cast<long long>(f->n) * f->h * f->w;
     if (plan->route == ROUTE_EMPTY) return launch_fill_empty(ctx, out, cnt, npx, erode ? f->L - 1 : 0, st);
+    if (plan->route == ROUTE_FFT32 || plan->route == ROUTE_FFT64)
+        return launch_fft(ctx, plan->fft, f, erode, out, cnt, opts ? opts->count_err : nullptr,
+                          (opts && (opts->flags & MORPH_F_VALIDATE)) ? 1 : 0, st);
 
     const DirectPlan& dp = plan->direct;
     void* ws = nullptr;
@@ -293,6 +335,7 @@ int morph_ctx_destroy(morph_ctx* ctx) {
     cudaDeviceSynchronize();
     ctx->plans.clear();
     ctx->aux_plans.clear();
+    ctx->route_cache.clear();
     for (auto& r : ctx->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -316,28 +359,53 @@ int morph_erode(morph_ctx* ctx, const morph_image* f, const morph_se* b, int32_t
 
 int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, int op, const morph_opts* opts,
                      morph_plan_info* out) {
-    if (!ctx) return inval("null context");
-    if (!out) return inval("null output");
+    if (!ctx || !out) return MORPH_E_INVAL;
     int rc = validate(f, b);
     if (rc) return rc;
     const int method = opts ? opts->method : MORPH_AUTO;
-    if (method != MORPH_AUTO && method != MORPH_DIRECT_FP8) return MORPH_E_UNSUPPORTED;
+    const bool unproven = opts && (opts->flags & MORPH_F_ALLOW_UNPROVEN_F32);
+    const int erode = op ? 1 : 0;
     EffSE e;
-    effective_se(b, op ? 1 : 0, &e);
-    std::shared_ptr<Plan> plan;
-    rc = get_plan(ctx, f, &e.se, op ? 1 : 0, ROUTE_DIRECT, &plan);
+    effective_se(b, erode, &e);
+    int route = ROUTE_DIRECT;
+    rc = choose_route(ctx, f, &e.se, erode, method, unproven, &route);
     if (rc) return rc;
     std::memset(out, 0, sizeof(*out));
-    const DirectPlan& d = plan->direct;
-    out->method = MORPH_DIRECT_FP8;
-    out->R = f->L + d.maxb;
-    out->taps = d.taps;
-    out->groups = d.G;
-    out->passes = d.n_pass;
-    out->tile_w = d.J;
-    out->tile_h = d.rows_n;
-    out->est_flop = d.issued_flop;
-    out->workspace_bytes = planes_bytes(f);
+    int taps = 0, maxb = 0;
+    for (int t = 0; t < b->kh * b->kw; ++t)
+        if (b->mask[t]) {
+            ++taps;
+            maxb = std::max(maxb, static_cast<int>(b->offset[t]));
+        }
+    out->R = f->L + maxb;
+    out->taps = taps;
+    FftPlan f32, f64;
+    if (taps > 0 && plan_fft_tiles(f, &e.se, 4, true, &f32) == MORPH_OK) out->f32_bound = f32.bound;
+    if (taps > 0 && plan_fft_tiles(f, &e.se, 8, true, &f64) == MORPH_OK) out->f64_bound = f64.bound;
+    if (route == ROUTE_DIRECT) {
+        std::shared_ptr<Plan> plan;
+        rc = get_plan(ctx, f, &e.se, erode, ROUTE_DIRECT, &plan);
+        if (rc) return rc;
+        const DirectPlan& d = plan->direct;
+        out->method = MORPH_DIRECT_FP8;
+        out->groups = d.G;
+        out->passes = d.n_pass;
+        out->tile_w = d.J;
+        out->tile_h = d.rows_n;
+        out->est_flop = d.issued_flop;
+        out->workspace_bytes = planes_bytes(f);
+    } else {
+        FftPlan q;
+        rc = plan_fft_tiles(f, &e.se, route == ROUTE_FFT32 ? 4 : 8, unproven, &q);
+        if (rc) return rc;
+        out->method = route == ROUTE_FFT32 ? MORPH_FFT_F32 : MORPH_FFT_F64;
+        out->fft_nx = q.ax.N;
+        out->fft_ny = q.ay.N;
+        out->tile_w = q.To_x;
+        out->tile_h = q.To_y;
+        out->est_flop = q.flop;
+        out->workspace_bytes = q.buf_bytes;
+    }
     return MORPH_OK;
 }
 

@@ -87,6 +87,32 @@ struct DirectPlan {
     ~DirectPlan();
 };
 
+// -------------------------------------------------------- FFT route (Step 2)
+struct FftAxis {
+    int N;         // transform length (2^a 3^b 5^c, <= 2048)
+    int nst;       // Stockham stages
+    int rad[16];   // radix of each stage (4, 2, 3, 5)
+};
+
+struct FftPlan {
+    int prec = 8;                 // 4 = FP32, 8 = FP64
+    int taps = 0, R = 0, K = 0;   // |B|, degrees, grey frequencies
+    int kh = 0, kw = 0, ry = 0, rx = 0;
+    int To_y = 0, To_x = 0, Rin_y = 0, Win_x = 0;
+    int tiles_y = 0, tiles_x = 0;
+    long long ntiles = 0;
+    int wave_tiles = 0, colgroup = 4;
+    size_t buf_bytes = 0;
+    double bound = 0;             // a-priori bound on |C - C_exact| for this precision
+    double flop = 0;
+    FftAxis ax, ay;
+    void* tw_x = nullptr;
+    void* tw_y = nullptr;
+    void* wr = nullptr;
+    void* S = nullptr;
+    ~FftPlan();
+};
+
 // ------------------------------------------------------------------- context
 struct Plan;
 
@@ -109,6 +135,7 @@ struct morph_ctx {
     uint64_t launches = 0;
     std::unordered_map<std::string, std::shared_ptr<morph::Plan>> plans;
     std::unordered_map<std::string, std::shared_ptr<void>> aux_plans;   // backward tap lists, ...
+    std::unordered_map<std::string, int> route_cache;                   // AUTO decisions
 };
 
 namespace morph {
@@ -134,5 +161,10 @@ int direct_stages();
 void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,
                          int32_t* out_cnt, long long tile_base, int* status);
 int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st);
+int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unproven, FftPlan* p);
+int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int prec, bool unproven, FftPlan* p);
+int launch_fft(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
+               float* count_err, int validate, cudaStream_t st);
+double fft_error_bound(const FftAxis& ax, const FftAxis& ay, double sqrtP, int taps, int K, double u);
 
 }  // namespace morph
