@@ -45,6 +45,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FFT-form comparison")
     ap.add_argument("--cpu-rows", type=int, default=48, help="oracle sample: rows per operation")
     return ap.parse_args()
 
@@ -275,6 +276,11 @@ def run_ours(args, ws, rank, local):
         e2e_ms = float(t.item())
     e2e = ws * px_per_step / (e2e_ms * 1e-3) / 1e6
 
+    # ---- the same workload through the FFT forms of Step 2 (FP64 and FP32)
+    forms = {"direct_fp8": {"value": value / ws, "ms_per_step": ms, "exact": True}}
+    if not args.no_forms:
+        forms.update(_time_forms(ctx, probs, f_dev, L, outs, px_per_step, stream, min(args.steps, 3)))
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -303,6 +309,8 @@ def run_ours(args, ws, rank, local):
                        "ops_per_step": 4, "l2": "working set > L2: 268 MB of FP8 indicator planes rewritten per op",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+            "forms": forms,
+            "vs_fp64_form": (value / ws / forms["fft_f64"]["value"]) if forms.get("fft_f64", {}).get("value") else None,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 only
@@ -310,6 +318,47 @@ def run_ours(args, ws, rank, local):
         line["cpu_baseline"] = _cpu_baseline(args, probs, outs)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _time_forms(ctx, probs, f_dev, L, ref_outs, px_per_step, stream, steps):
+    """Mpix/s of the FFT forms on the same four operations, each checked
+    bit-exact against the FP8 route's outputs (per-GPU numbers)."""
+    import torch
+    res = {}
+    for name, method, kw in (("fft_f64", "fft_f64", {}),
+                             ("fft_f32", "fft_f32", {"allow_unproven_f32": True})):
+        outs = [torch.empty_like(o) for o in ref_outs]
+        err = torch.zeros(1, dtype=torch.float32, device=f_dev.device)
+
+        def step():
+            for p, o in zip(probs, outs):
+                (ctx.dilate if p.op == "dilate" else ctx.erode)(f_dev, L, p.se, method=method, out=o, **kw)
+
+        step()                                   # plans (SE spectra, tables) + warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        exact = all(bool(torch.equal(o, r)) for o, r in zip(outs, ref_outs))
+        worst = 0.0
+        bounds = []
+        for p in probs:                          # measured max |C - rint C| over every degree
+            err.zero_()
+            o = torch.empty_like(ref_outs[0])
+            (ctx.dilate if p.op == "dilate" else ctx.erode)(f_dev, L, p.se, method=method, out=o, count_err=err, **kw)
+            torch.cuda.synchronize()
+            worst = max(worst, float(err.item()))
+            info = ctx.plan(f_dev, L, p.se, op=0 if p.op == "dilate" else 1, method=method, **kw)
+            bounds.append(info.f32_bound if method == "fft_f32" else info.f64_bound)
+        ctx.check()
+        res[name] = {"value": px_per_step / (ms * 1e-3) / 1e6, "ms_per_step": ms, "exact": exact,
+                     "max_count_err": worst, "a_priori_bound_max": max(bounds),
+                     "proven": max(bounds) < 0.5}
+    return res
 
 
 def _cpu_baseline(args, probs, outs):

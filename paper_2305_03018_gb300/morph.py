@@ -320,7 +320,7 @@ class Context:
     def erode(self, f, L, se, method="auto", count=False, stream=None, **kw):
         return self._run(1, f, L, se, method, count, stream, **kw)
 
-    def plan(self, f, L, se, op=0, method="auto", allow_unproven_f32=False):
+    def plan(self, f, L, se, op=0, method="auto", allow_unproven_f32=False, **_):
         img = make_image(f, L)
         sv = se_view(se)
         return morph_plan_query(self.handle, img, sv.c, op, make_opts(method, allow_unproven_f32))
