@@ -163,19 +163,28 @@ typedef struct {
     int32_t *out_count;      /* nullable */
 } morph_problem;
 
-/* Run `n` problems: all FP8-direct problems in one persistent launch, FFT
- * problems after it, on `stream`.  Plans are built on first use. */
+/* Run `n` problems on `stream`: one encoder launch and one persistent
+ * tcgen05 launch cover every problem on the FP8 direct route (tiles of the
+ * most expensive problems first); problems on an FFT route follow with their
+ * own launches.  opts applies to every problem (AUTO: the planner chooses per
+ * problem); opts->count_err, if given, receives the max over the FFT problems.
+ * Plans are built on first use.  The problem descriptors are copied to the
+ * context's workspace in stream order before the kernels are queued. */
 int morph_run_batch(morph_ctx *ctx, const morph_problem *p, int n, const morph_opts *opts,
                     morph_stream_t stream);
 
 typedef struct morph_batch morph_batch;
 
-/* Plan the batch once and capture its launches into a CUDA graph.  The
- * problems' device pointers are baked into the graph: replays read the
- * current contents of the same buffers. */
+/* Plan the batch once and capture its launches into a CUDA graph with a
+ * workspace of its own.  The problems' device pointers are baked into the
+ * graph: each morph_batch_launch replays it on `stream`, reading the current
+ * contents of the same buffers.  morph_batch_destroy waits for the device
+ * and frees the graph and its workspace. */
 int morph_batch_capture(morph_ctx *ctx, const morph_problem *p, int n, const morph_opts *opts,
                         morph_batch **out);
+/* Replay a captured batch on `stream` (asynchronous). */
 int morph_batch_launch(morph_batch *b, morph_stream_t stream);
+/* Wait for the device, then free a captured batch. */
 int morph_batch_destroy(morph_batch *b);
 
 /* Synchronize `stream`, then return (and clear) the device error word:

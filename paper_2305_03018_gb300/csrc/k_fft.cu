@@ -728,14 +728,19 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
     return MORPH_OK;
 }
 
+int launch_fft_in(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
+                  float* count_err, int validate, void* buf, cudaStream_t st) {
+    if (p.prec == 4) return launch_fft_t<float>(ctx, p, f, erode, out, cnt, count_err, validate, buf, st);
+    return launch_fft_t<double>(ctx, p, f, erode, out, cnt, count_err, validate, buf, st);
+}
+
 int launch_fft(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
                float* count_err, int validate, cudaStream_t st) {
     void* buf = nullptr;
     int rc = ctx_workspace(ctx, p.buf_bytes, &buf);
     if (rc) return rc;
     if (count_err) MORPH_CUDA_TRY(cudaMemsetAsync(count_err, 0, sizeof(float), st));
-    if (p.prec == 4) return launch_fft_t<float>(ctx, p, f, erode, out, cnt, count_err, validate, buf, st);
-    return launch_fft_t<double>(ctx, p, f, erode, out, cnt, count_err, validate, buf, st);
+    return launch_fft_in(ctx, p, f, erode, out, cnt, count_err, validate, buf, st);
 }
 
 }  // namespace morph

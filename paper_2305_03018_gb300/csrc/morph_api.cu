@@ -112,13 +112,6 @@ int ctx_workspace(morph_ctx* ctx, size_t bytes, void** out) {
 }
 
 // ------------------------------------------------------------------ plans
-enum Route { ROUTE_EMPTY = 0, ROUTE_DIRECT = 1, ROUTE_FFT32 = 2, ROUTE_FFT64 = 3 };
-
-struct Plan {
-    int route = ROUTE_EMPTY;
-    DirectPlan direct;
-    FftPlan fft;
-};
 
 // SE after the erosion-by-duality reflection (Sec. 2.1): b_reflected(y) = b(-y),
 // i.e. the box is flipped in both axes and the origin moves to (kh-1-oy, kw-1-ox).
@@ -206,7 +199,7 @@ static int get_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, in
     return MORPH_OK;
 }
 
-static size_t planes_bytes(const morph_image* f) {
+size_t planes_bytes(const morph_image* f) {
     const size_t w_pad = (static_cast<size_t>(f->w) + 15) & ~size_t(15);
     return static_cast<size_t>(f->n) * f->h * f->L * w_pad;
 }
@@ -242,10 +235,9 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
     return MORPH_OK;
 }
 
-static int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
-                   const morph_opts* opts, cudaStream_t st) {
+int prepare_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, const morph_opts* opts,
+                    std::shared_ptr<Plan>* plan) {
     if (!ctx) return inval("null context");
-    if (!out) return inval("null output");
     int rc = validate(f, b);
     if (rc) return rc;
     const int method = opts ? opts->method : MORPH_AUTO;
@@ -255,8 +247,14 @@ static int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int 
     int route = ROUTE_DIRECT;
     rc = choose_route(ctx, f, &e.se, erode, method, unproven, &route);
     if (rc) return rc;
+    return get_plan(ctx, f, &e.se, erode, route, plan, route == ROUTE_FFT32 && unproven);
+}
+
+static int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
+                   const morph_opts* opts, cudaStream_t st) {
+    if (!out) return inval("null output");
     std::shared_ptr<Plan> plan;
-    rc = get_plan(ctx, f, &e.se, erode, route, &plan, route == ROUTE_FFT32 && unproven);
+    int rc = prepare_problem(ctx, f, b, erode, opts, &plan);
     if (rc) return rc;
     const long long npx = static_cast<long long>(f->n) * f->h * f->w;
     if (plan->route == ROUTE_EMPTY) return launch_fill_empty(ctx, out, cnt, npx, erode ? f->L - 1 : 0, st);

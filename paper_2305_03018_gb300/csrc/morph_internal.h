@@ -113,8 +113,14 @@ struct FftPlan {
     ~FftPlan();
 };
 
-// ------------------------------------------------------------------- context
-struct Plan;
+// ------------------------------------------------------------------- plans
+enum Route { ROUTE_EMPTY = 0, ROUTE_DIRECT = 1, ROUTE_FFT32 = 2, ROUTE_FFT64 = 3 };
+
+struct Plan {
+    int route = ROUTE_EMPTY;
+    DirectPlan direct;
+    FftPlan fft;
+};
 
 }  // namespace morph
 
@@ -161,10 +167,16 @@ int direct_stages();
 void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,
                          int32_t* out_cnt, long long tile_base, int* status);
 int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st);
+// validation, erosion reflection, route choice and (cached) plan of one problem
+int prepare_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, const morph_opts* opts,
+                    std::shared_ptr<Plan>* plan);
+size_t planes_bytes(const morph_image* f);
 int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unproven, FftPlan* p);
 int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int prec, bool unproven, FftPlan* p);
 int launch_fft(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
                float* count_err, int validate, cudaStream_t st);
+int launch_fft_in(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
+                  float* count_err, int validate, void* buf, cudaStream_t st);
 double fft_error_bound(const FftAxis& ax, const FftAxis& ay, double sqrtP, int taps, int K, double u);
 
 }  // namespace morph

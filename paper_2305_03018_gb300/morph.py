@@ -325,6 +325,35 @@ class Context:
         sv = se_view(se)
         return morph_plan_query(self.handle, img, sv.c, op, make_opts(method, allow_unproven_f32))
 
+    # -- batches ---------------------------------------------------------------
+    def _problems(self, items):
+        """items: (f, L, se, op, out, out_count-or-None) tuples of CUDA tensors."""
+        import torch
+        keep, probs = [], []
+        for (f, L, se, op, out, cnt) in items:
+            img = make_image(f, L)
+            sv = se_view(se)
+            pr = morph_problem()
+            pr.f = img
+            pr.se = sv.c
+            pr.op = 0 if op in (0, "dilate") else 1
+            pr.out = out.data_ptr()
+            pr.out_count = cnt.data_ptr() if cnt is not None else None
+            keep.append(sv)
+            probs.append(pr)
+        return probs, keep
+
+    def run_batch(self, items, method="auto", stream=None, allow_unproven_f32=False, count_err=None):
+        probs, keep = self._problems(items)
+        opts = make_opts(method, allow_unproven_f32, count_err is not None, count_err)
+        st = stream if stream is not None else current_stream_handle(self.device)
+        check(morph_run_batch(self.handle, probs, opts, st), "morph_run_batch")
+
+    def capture_batch(self, items, method="auto", allow_unproven_f32=False):
+        probs, keep = self._problems(items)
+        h = morph_batch_capture(self.handle, probs, make_opts(method, allow_unproven_f32))
+        return CapturedBatch(h, keep)
+
     def check(self, stream=None):
         st = stream if stream is not None else current_stream_handle(self.device)
         check(morph_stream_check(self.handle, st), "morph_stream_check")
@@ -337,6 +366,29 @@ class Context:
 
     def profile_read(self):
         return morph_profile_read(self.handle)
+
+
+class CapturedBatch:
+    """A batch planned once and recorded into a CUDA graph (morph_batch_capture)."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        st = stream if stream is not None else current_stream_handle()
+        check(morph_batch_launch(self.handle, st), "morph_batch_launch")
+
+    def close(self):
+        if self.handle:
+            morph_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _contexts = {}

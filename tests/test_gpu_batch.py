@@ -1,0 +1,93 @@
+"""GPU batches (one persistent launch for the FP8 route, graph capture)
+against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_03018_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2305_03018_gb300.morph import get_context
+    return get_context(0)
+
+
+def _items(probs):
+    items, outs = [], []
+    for p in probs:
+        ft = torch.from_numpy(np.ascontiguousarray(p.f)).cuda()
+        o = torch.full(ft.shape, -99, dtype=torch.int32, device="cuda")
+        c = torch.full(ft.shape, -99, dtype=torch.int32, device="cuda")
+        items.append((ft, p.L, p.se, p.op, o, c))
+        outs.append((o, c))
+    return items, outs
+
+
+def _check(p, o, c, rows=None):
+    fn = oracle.dilate if p.op == "dilate" else oracle.erode
+    H = p.f.shape[1]
+    r = rows if rows is not None else (0, H)
+    D, cD = fn(p.f, p.L, p.se.mask, p.se.offset, p.se.origin, rows=r, nthreads=0)
+    got_d = o.cpu().numpy()[:, r[0]:r[1]]
+    got_c = c.cpu().numpy()[:, r[0]:r[1]]
+    assert np.array_equal(got_d, D[:, r[0]:r[1]]), p.name
+    assert np.array_equal(got_c, cD[:, r[0]:r[1]]), p.name
+
+
+def test_small_heterogeneous_batch(ctx):
+    probs = wl.c5_batch(n=24, seed=55, max_side=160)
+    items, outs = _items(probs)
+    ctx.run_batch(items, method="direct_fp8")
+    ctx.check()
+    for p, (o, c) in zip(probs, outs):
+        _check(p, o, c)
+
+
+def test_auto_batch_mixes_routes(ctx):
+    probs = wl.c5_batch(n=16, seed=56, max_side=120)
+    probs.append(wl.Problem(wl.uniform_image(wl.rng(1), (1, 90, 70), 16), 16, wl.se_flat_square(3), "erode", "tiny"))
+    items, outs = _items(probs)
+    ctx.run_batch(items, method="auto")
+    ctx.check()
+    for p, (o, c) in zip(probs, outs):
+        _check(p, o, c)
+
+
+def test_captured_graph_replays_current_inputs(ctx):
+    probs = wl.c5_batch(n=12, seed=57, max_side=140)
+    items, outs = _items(probs)
+    b = ctx.capture_batch(items, method="direct_fp8")
+    b.launch()
+    ctx.check()
+    for p, (o, c) in zip(probs, outs):
+        _check(p, o, c)
+    # new pixel values in the same buffers: the replay must see them
+    g = wl.rng(58)
+    for p, it in zip(probs, items):
+        p.f = g.integers(0, p.L, size=p.f.shape).astype(p.f.dtype)
+        it[0].copy_(torch.from_numpy(p.f))
+    b.launch()
+    ctx.check()
+    for p, (o, c) in zip(probs, outs):
+        _check(p, o, c)
+    b.close()
+
+
+def test_c5_full_batch_sampled(ctx):
+    probs = wl.c5_batch()                       # 512 problems, sides up to 1024
+    items, outs = _items(probs)
+    b = ctx.capture_batch(items)
+    b.launch()
+    ctx.check()
+    g = wl.rng(59)
+    for k in g.choice(len(probs), size=40, replace=False):
+        p = probs[int(k)]
+        o, c = outs[int(k)]
+        H = p.f.shape[1]
+        r0 = int(g.integers(0, H - 2))
+        _check(p, o, c, rows=(r0, r0 + 2))
+    b.close()
