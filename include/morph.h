@@ -105,7 +105,8 @@ typedef struct {
     int method;              /* enum morph_method actually used */
     int R;                   /* number of degrees: L + max b */
     int taps;                /* |B| */
-    double f32_bound;        /* a-priori bound on the FP32 FFT count error */
+    double f32_bound;        /* a-priori bound on the FP32 FFT count error of the tiling an
+                                FP32 request runs (< 0.5: proven exact; else no tiling is) */
     double f64_bound;        /* the same bound for FP64 */
     int fft_nx, fft_ny;      /* FFT sizes of the FFT routes */
     int groups, passes;      /* direct route: offset levels stacked per pass, passes */

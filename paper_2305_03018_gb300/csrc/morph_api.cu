@@ -377,9 +377,17 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         }
     out->R = f->L + maxb;
     out->taps = taps;
+    // bound of the tiling an FP32 (FP64) request would run: the cheapest tiling
+    // whose bound is below 0.5 if one exists, else the cheapest tiling
     FftPlan f32, f64;
-    if (taps > 0 && plan_fft_tiles(f, &e.se, 4, true, &f32) == MORPH_OK) out->f32_bound = f32.bound;
-    if (taps > 0 && plan_fft_tiles(f, &e.se, 8, true, &f64) == MORPH_OK) out->f64_bound = f64.bound;
+    if (taps > 0) {
+        if (plan_fft_tiles(f, &e.se, 4, false, &f32) == MORPH_OK ||
+            plan_fft_tiles(f, &e.se, 4, true, &f32) == MORPH_OK)
+            out->f32_bound = f32.bound;
+        if (plan_fft_tiles(f, &e.se, 8, false, &f64) == MORPH_OK ||
+            plan_fft_tiles(f, &e.se, 8, true, &f64) == MORPH_OK)
+            out->f64_bound = f64.bound;
+    }
     if (route == ROUTE_DIRECT) {
         std::shared_ptr<Plan> plan;
         rc = get_plan(ctx, f, &e.se, erode, ROUTE_DIRECT, &plan);
