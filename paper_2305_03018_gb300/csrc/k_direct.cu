@@ -30,7 +30,11 @@
 //   warp 1   : TMEM allocator + MMA issuer (one lane), tcgen05.mma kind::f8f6f4;
 //   warps 2-5: epilogue (TMEM -> registers -> SMEM reduction -> int32 output).
 // Two TMEM accumulators (2 x 256 columns) let the epilogue of one unit
-// overlap the MMAs of the next.
+// overlap the MMAs of the next.  When two horizontally adjacent tiles fit in
+// one 128-byte K window (2 J + kw - 1 <= 128), a unit holds both (T = 2):
+// each A / B stage feeds the MMAs of both tiles, the second reading B from a
+// start address J bytes further, which halves the operand bytes per MMA; the
+// two accumulators then belong to the one unit.
 #include <algorithm>
 #include <cstring>
 
@@ -84,7 +88,7 @@ __device__ __forceinline__ TileCoord direct_tile(const DirectProblemDev* P, long
     c.n = static_cast<int>(lt / per_img);
     const int rem = static_cast<int>(lt % per_img);
     c.i0 = (rem / P->tiles_x) * P->rows_n;
-    c.j0 = (rem % P->tiles_x) * P->J - P->e;
+    c.j0 = (rem % P->tiles_x) * P->J * P->T - P->e;
     return c;
 }
 
@@ -176,16 +180,25 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
     } else if (warp == 1 && lane == 0) {
         // -------------------------------------------------------- MMA issuer
         const uint32_t idesc = idesc_e4m3_f32(kDirectM, kDirectN);
-        uint32_t it = 0, unit = 0;
+        uint32_t it = 0;
+        uint32_t uses[2] = {0u, 0u};   // completed claims of each TMEM accumulator slot
+        uint32_t next_slot = 0;
         bool ok = true;
         for (long long t = blockIdx.x; ok && t < dl.total_tiles; t += gridDim.x) {
             const DirectProblemDev* P = direct_find(dl, t);
             const int* rb = P->meta;
+            const int T = P->T;
             for (int p = 0; ok && p < P->n_pass; ++p) {
-                const uint32_t buf = unit & 1u;
-                if (!mbar_wait(smem_u32(&tail->tempty[buf]), ((unit >> 1) & 1u) ^ 1u, abort_flag, dl.err)) { ok = false; break; }
+                // a unit claims one slot (T = 1, alternating) or both (T = 2)
+                const uint32_t s0 = (T == 2) ? 0u : next_slot;
+                next_slot = (T == 2) ? 0u : (next_slot ^ 1u);
+                for (int tt = 0; ok && tt < T; ++tt) {
+                    const uint32_t sl = s0 + tt;
+                    if (!mbar_wait(smem_u32(&tail->tempty[sl]), (uses[sl] & 1u) ^ 1u, abort_flag, dl.err)) ok = false;
+                }
+                if (!ok) break;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + buf * kDirectN;
+                const uint32_t d_tmem = tmem_base + s0 * kDirectN;
                 uint32_t acc = 0;
                 for (int q = rb[p]; ok && q < rb[p + 1]; ++q) {
                     for (int kc = 0; kc < P->nk; ++kc) {
@@ -197,17 +210,23 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                         const uint64_t adesc = umma_desc_sw128(smem_u32(sa));
                         const uint64_t bdesc = umma_desc_sw128(smem_u32(sa + kStageA));
                         const int nks = min(4, P->ksteps - 4 * kc);
-                        for (int ks = 0; ks < nks; ++ks) {
-                            // advance the start address by 32 B of K inside the 128-B swizzled rows
-                            tc_mma_f8(d_tmem, adesc + 2ull * ks, bdesc + 2ull * ks, idesc, acc);
-                            acc = 1;
+                        for (int tt = 0; tt < T; ++tt) {
+                            // tile tt reads B from J * tt bytes further along K (16-byte units)
+                            const uint64_t boff = static_cast<uint64_t>(tt * P->J) >> 4;
+                            for (int ks = 0; ks < nks; ++ks) {
+                                // advance the start address by 32 B of K inside the 128-B swizzled rows
+                                tc_mma_f8(d_tmem + tt * kDirectN, adesc + 2ull * ks, bdesc + boff + 2ull * ks, idesc,
+                                          (acc != 0u || ks > 0) ? 1u : 0u);
+                            }
                         }
+                        acc = 1;
                         tc_commit(smem_u32(&tail->empty[s]));
                         ++it;
                     }
                 }
-                if (ok) tc_commit(smem_u32(&tail->tfull[buf]));
-                ++unit;
+                if (ok)
+                    for (int tt = 0; tt < T; ++tt) tc_commit(smem_u32(&tail->tfull[s0 + tt]));
+                for (int tt = 0; tt < T; ++tt) ++uses[s0 + tt];
             }
         }
         if (!ok) {
@@ -219,79 +238,89 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         const int quarter = warp & 3;                 // TMEM lane quarter this warp may access
         const int m = quarter * 32 + lane;            // accumulator row = (group, column)
         const int et = threadIdx.x - 64;              // 0..127
-        uint32_t unit = 0;
+        uint32_t uses[2] = {0u, 0u};   // same slot-claim sequence as the MMA issuer
+        uint32_t next_slot = 0;
         for (long long t = blockIdx.x; t < dl.total_tiles; t += gridDim.x) {
             const DirectProblemDev* P = direct_find(dl, t);
             const TileCoord tc = direct_tile(P, t);
-            const int J = P->J, G = P->G, rows_n = P->rows_n, Lpad = P->Lpad;
+            const int J = P->J, G = P->G, rows_n = P->rows_n, Lpad = P->Lpad, T = P->T;
             const int g = m / J;
             const int* gw = P->meta + (P->n_pass + 1);
             bool failed = false;
             for (int p = 0; p < P->n_pass; ++p) {
-                const uint32_t buf = unit & 1u;
-                const bool ok = mbar_wait(smem_u32(&tail->tfull[buf]), (unit >> 1) & 1u, abort_flag, dl.err);
+                const uint32_t s0 = (T == 2) ? 0u : next_slot;
+                next_slot = (T == 2) ? 0u : (next_slot ^ 1u);
+                bool ok = true;
+                for (int tt = 0; tt < T; ++tt)
+                    ok = ok && mbar_wait(smem_u32(&tail->tfull[s0 + tt]), uses[s0 + tt] & 1u, abort_flag, dl.err);
                 if (epi_any_failed(!ok)) { failed = true; break; }
                 tc_fence_after();
                 const int wg = (g < G) ? gw[p * 8 + g] : 0;
-                const uint32_t trow = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + buf * kDirectN;
-                for (int tr = 0; tr < rows_n; ++tr) {
-                    const uint32_t col0 = static_cast<uint32_t>(tr * Lpad);
-                    int top = -1;
-                    float cnt = 0.f;
-                    if (Lpad == 16) {
-                        float v[16];
-                        tmem_ld_32x32b_x16(trow + col0, v);
-                        tc_wait_ld();
-#pragma unroll
-                        for (int k = 0; k < 16; ++k)
-                            if (v[k] > 0.5f) { top = k; cnt = v[k]; }
-                    } else {
-                        for (int c = Lpad / 32 - 1; c >= 0; --c) {
-                            if (__all_sync(0xffffffffu, top >= 0)) break;
-                            float v[32];
-                            tmem_ld_32x32b_x32(trow + col0 + 32u * c, v);
+                for (int tt = 0; tt < T; ++tt) {
+                    const uint32_t trow =
+                        tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + (s0 + tt) * kDirectN;
+                    for (int tr = 0; tr < rows_n; ++tr) {
+                        const uint32_t col0 = static_cast<uint32_t>(tr * Lpad);
+                        int top = -1;
+                        float cnt = 0.f;
+                        if (Lpad == 16) {
+                            float v[16];
+                            tmem_ld_32x32b_x16(trow + col0, v);
                             tc_wait_ld();
-                            if (top < 0) {
 #pragma unroll
-                                for (int k = 0; k < 32; ++k)
-                                    if (v[k] > 0.5f) { top = 32 * c + k; cnt = v[k]; }
+                            for (int k = 0; k < 16; ++k)
+                                if (v[k] > 0.5f) { top = k; cnt = v[k]; }
+                        } else {
+                            for (int c = Lpad / 32 - 1; c >= 0; --c) {
+                                if (__all_sync(0xffffffffu, top >= 0)) break;
+                                float v[32];
+                                tmem_ld_32x32b_x32(trow + col0 + 32u * c, v);
+                                tc_wait_ld();
+                                if (top < 0) {
+#pragma unroll
+                                    for (int k = 0; k < 32; ++k)
+                                        if (v[k] > 0.5f) { top = 32 * c + k; cnt = v[k]; }
+                                }
+                            }
+                        }
+                        red[tr * 128 + m] =
+                            (top >= 0) ? make_int2(top + wg, __float2int_rn(cnt)) : make_int2(-1, 0);
+                    }
+                    // this accumulator's TMEM reads are done: hand it back
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&tail->tempty[s0 + tt]));
+                    epi_bar();
+                    const int pairs = rows_n * J;
+                    for (int idx = et; idx < pairs; idx += 128) {
+                        const int tr = idx / J, jl = idx - tr * J;
+                        int best = -1, bc = 0;
+                        for (int gg = 0; gg < G; ++gg) {
+                            const int2 e = red[tr * 128 + gg * J + jl];
+                            if (e.x > best) { best = e.x; bc = e.y; }
+                            else if (e.x == best && e.x >= 0) bc += e.y;
+                        }
+                        int2 cur = make_int2(best, bc);
+                        const int ri = tt * pairs + idx;
+                        if (p > 0) {
+                            const int2 prev = run[ri];
+                            if (prev.x > cur.x) cur = prev;
+                            else if (prev.x == cur.x && cur.x >= 0) cur.y += prev.y;
+                        }
+                        run[ri] = cur;
+                        if (p == P->n_pass - 1) {
+                            const int i = tc.i0 + tr, j = tc.j0 + tt * J + jl;
+                            if (i < P->h && j >= 0 && j < P->w) {
+                                const int dval = cur.x < 0 ? 0 : cur.x;
+                                const long long o = (static_cast<long long>(tc.n) * P->h + i) * P->w + j;
+                                P->out[o] = P->erode ? (P->L - 1 - dval) : dval;
+                                if (P->out_cnt) P->out_cnt[o] = cur.x < 0 ? 0 : cur.y;
                             }
                         }
                     }
-                    red[tr * 128 + m] = (top >= 0) ? make_int2(top + wg, __float2int_rn(cnt)) : make_int2(-1, 0);
+                    epi_bar();
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&tail->tempty[buf]));
-                epi_bar();
-                const int pairs = rows_n * J;
-                for (int idx = et; idx < pairs; idx += 128) {
-                    const int tr = idx / J, jl = idx - tr * J;
-                    int best = -1, bc = 0;
-                    for (int gg = 0; gg < G; ++gg) {
-                        const int2 e = red[tr * 128 + gg * J + jl];
-                        if (e.x > best) { best = e.x; bc = e.y; }
-                        else if (e.x == best && e.x >= 0) bc += e.y;
-                    }
-                    int2 cur = make_int2(best, bc);
-                    if (p > 0) {
-                        const int2 prev = run[idx];
-                        if (prev.x > cur.x) cur = prev;
-                        else if (prev.x == cur.x && cur.x >= 0) cur.y += prev.y;
-                    }
-                    run[idx] = cur;
-                    if (p == P->n_pass - 1) {
-                        const int i = tc.i0 + tr, j = tc.j0 + jl;
-                        if (i < P->h && j >= 0 && j < P->w) {
-                            const int dval = cur.x < 0 ? 0 : cur.x;
-                            const long long o = (static_cast<long long>(tc.n) * P->h + i) * P->w + j;
-                            P->out[o] = P->erode ? (P->L - 1 - dval) : dval;
-                            if (P->out_cnt) P->out_cnt[o] = cur.x < 0 ? 0 : cur.y;
-                        }
-                    }
-                }
-                epi_bar();
-                ++unit;
+                for (int tt = 0; tt < T; ++tt) ++uses[s0 + tt];
             }
             if (failed) break;
         }
@@ -391,9 +420,12 @@ int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, 
     p->ksteps = (p->J + kw - 1 + 31) / 32;
     p->nk = (p->J + kw - 1 + 127) / 128;
     p->n_pass = (p->n_levels + p->G - 1) / p->G;
+    // two tiles per unit when both windows fit one 128-byte stage and the image is wide enough
+    // (the second tile's K-steps read up to J + 32 ksteps bytes into the 128-byte rows)
+    p->T = (2 * p->J + kw - 1 <= 128 && p->J + 32 * p->ksteps <= 128 && f->w > p->J) ? 2 : 1;
     const int a = (((kw - 1 - se->ox) % 16) + 16) % 16;
     p->e = (16 - a) % 16;
-    p->tiles_x = (f->w + p->e + p->J - 1) / p->J;
+    p->tiles_x = (f->w + p->e + p->T * p->J - 1) / (p->T * p->J);
     p->tiles_y = (f->h + p->rows_n - 1) / p->rows_n;
     p->tiles = static_cast<long long>(f->n) * p->tiles_x * p->tiles_y;
     // meta: pass_row_begin[n_pass + 1], group_w[n_pass * 8], rows[]
@@ -423,7 +455,7 @@ int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, 
     p->meta.insert(p->meta.end(), gw.begin(), gw.end());
     p->meta.insert(p->meta.end(), rows.begin(), rows.end());
     p->toeplitz_blocks = p->active_rows_total * p->nk;
-    p->issued_flop = static_cast<double>(p->tiles) * static_cast<double>(p->active_rows_total) * p->ksteps * 2.0 *
+    p->issued_flop = static_cast<double>(p->tiles) * p->T * static_cast<double>(p->active_rows_total) * p->ksteps * 2.0 *
                      kDirectM * kDirectN * 32.0;
 
     // device copies and the Toeplitz blocks
@@ -492,6 +524,7 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
     d->ox = p.ox;
     d->e = p.e;
     d->erode = p.erode;
+    d->T = p.T;
     d->tiles_x = p.tiles_x;
     d->tiles_y = p.tiles_y;
     d->tile_base = tile_base;

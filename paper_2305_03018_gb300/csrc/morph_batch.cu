@@ -73,11 +73,11 @@ int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts*
         else if (it.plan->route == ROUTE_EMPTY) b->empty_items.push_back(i);
         else b->fft_items.push_back(i);
     }
-    // heaviest tiles first: MMA work per tile = active SE rows x K-steps
+    // heaviest units first: MMA work per unit = active SE rows x K-steps x tiles
     std::stable_sort(b->direct_order.begin(), b->direct_order.end(), [&](int a, int c) {
         const DirectPlan& x = b->items[a].plan->direct;
         const DirectPlan& y = b->items[c].plan->direct;
-        return x.active_rows_total * x.ksteps > y.active_rows_total * y.ksteps;
+        return x.active_rows_total * x.ksteps * x.T > y.active_rows_total * y.ksteps * y.T;
     });
     size_t off = 0;
     b->jobs_off = off;

@@ -57,7 +57,8 @@ struct DirectProblemDev {
     int Lpad, rows_n, J, G;
     int n_pass, nk, ksteps, kw;
     int oy, ox, e, erode;
-    int tiles_x, tiles_y;
+    int T;                  // horizontally adjacent tiles sharing each A/B stage (1 or 2)
+    int tiles_x, tiles_y;   // units (of T tiles) across, tile rows down
     long long tile_base;    // first global tile of this problem
     long long tiles;        // tiles of this problem
 };
@@ -71,7 +72,7 @@ struct DirectLaunch {
 };
 
 struct DirectPlan {
-    int L = 0, Lpad = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0;
+    int L = 0, Lpad = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0, T = 1;
     int kh = 0, kw = 0, oy = 0, ox = 0, e = 0, erode = 0;
     int h = 0, w = 0, nimg = 0, w_pad = 0;
     int tiles_x = 0, tiles_y = 0;
