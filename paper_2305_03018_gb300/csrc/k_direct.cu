@@ -105,6 +105,9 @@ __device__ __forceinline__ bool epi_any_failed(bool failed) {
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+// TT = 1 or 2: every problem of the launch has that many tiles per unit (the
+// compiler specialises the MMA issue loop); TT = 0: read T per problem.
+template <int TT>
 __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_constant__ DirectLaunch dl) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -181,27 +184,29 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         // -------------------------------------------------------- MMA issuer
         const uint32_t idesc = idesc_e4m3_f32(kDirectM, kDirectN);
         uint32_t it = 0;
-        uint32_t uses[2] = {0u, 0u};   // completed claims of each TMEM accumulator slot
+        uint32_t use0 = 0u, use1 = 0u;   // completed claims of TMEM accumulator slots 0 and 1
         uint32_t next_slot = 0;
         bool ok = true;
         for (long long t = blockIdx.x; ok && t < dl.total_tiles; t += gridDim.x) {
             const DirectProblemDev* P = direct_find(dl, t);
             const int* rb = P->meta;
-            const int T = P->T;
+            const bool two = (TT == 0) ? (P->T == 2) : (TT == 2);
+            const uint64_t boff1 = static_cast<uint64_t>(P->J) >> 4;   // second tile: J bytes further along K
+            const int ksteps = P->ksteps, nk = P->nk;
             for (int p = 0; ok && p < P->n_pass; ++p) {
                 // a unit claims one slot (T = 1, alternating) or both (T = 2)
-                const uint32_t s0 = (T == 2) ? 0u : next_slot;
-                next_slot = (T == 2) ? 0u : (next_slot ^ 1u);
-                for (int tt = 0; ok && tt < T; ++tt) {
-                    const uint32_t sl = s0 + tt;
-                    if (!mbar_wait(smem_u32(&tail->tempty[sl]), (uses[sl] & 1u) ^ 1u, abort_flag, dl.err)) ok = false;
-                }
+                const uint32_t s0 = two ? 0u : next_slot;
+                next_slot = two ? 0u : (next_slot ^ 1u);
+                if (two || s0 == 0u)
+                    ok = mbar_wait(smem_u32(&tail->tempty[0]), (use0 & 1u) ^ 1u, abort_flag, dl.err);
+                if (ok && (two || s0 == 1u))
+                    ok = mbar_wait(smem_u32(&tail->tempty[1]), (use1 & 1u) ^ 1u, abort_flag, dl.err);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + s0 * kDirectN;
                 uint32_t acc = 0;
                 for (int q = rb[p]; ok && q < rb[p + 1]; ++q) {
-                    for (int kc = 0; kc < P->nk; ++kc) {
+                    for (int kc = 0; kc < nk; ++kc) {
                         const int s = static_cast<int>(it % kStages);
                         const uint32_t ph = (it / kStages) & 1u;
                         if (!mbar_wait(smem_u32(&tail->full[s]), ph, abort_flag, dl.err)) { ok = false; break; }
@@ -209,24 +214,31 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                         const uint8_t* sa = base + s * kStageBytes;
                         const uint64_t adesc = umma_desc_sw128(smem_u32(sa));
                         const uint64_t bdesc = umma_desc_sw128(smem_u32(sa + kStageA));
-                        const int nks = min(4, P->ksteps - 4 * kc);
-                        for (int tt = 0; tt < T; ++tt) {
-                            // tile tt reads B from J * tt bytes further along K (16-byte units)
-                            const uint64_t boff = static_cast<uint64_t>(tt * P->J) >> 4;
+                        const int nks = min(4, ksteps - 4 * kc);
+                        // advance the start addresses by 32 B of K inside the 128-B swizzled rows
+                        if (two) {
                             for (int ks = 0; ks < nks; ++ks) {
-                                // advance the start address by 32 B of K inside the 128-B swizzled rows
-                                tc_mma_f8(d_tmem + tt * kDirectN, adesc + 2ull * ks, bdesc + boff + 2ull * ks, idesc,
-                                          (acc != 0u || ks > 0) ? 1u : 0u);
+                                tc_mma_f8(d_tmem, adesc + 2ull * ks, bdesc + 2ull * ks, idesc, acc);
+                                tc_mma_f8(d_tmem + kDirectN, adesc + 2ull * ks, bdesc + boff1 + 2ull * ks, idesc, acc);
+                                acc = 1;
+                            }
+                        } else {
+#pragma unroll 4
+                            for (int ks = 0; ks < nks; ++ks) {
+                                tc_mma_f8(d_tmem, adesc + 2ull * ks, bdesc + 2ull * ks, idesc, acc);
+                                acc = 1;
                             }
                         }
-                        acc = 1;
                         tc_commit(smem_u32(&tail->empty[s]));
                         ++it;
                     }
                 }
-                if (ok)
-                    for (int tt = 0; tt < T; ++tt) tc_commit(smem_u32(&tail->tfull[s0 + tt]));
-                for (int tt = 0; tt < T; ++tt) ++uses[s0 + tt];
+                if (ok) {
+                    tc_commit(smem_u32(&tail->tfull[s0]));
+                    if (two) tc_commit(smem_u32(&tail->tfull[1]));
+                }
+                if (two || s0 == 0u) ++use0;
+                if (two || s0 == 1u) ++use1;
             }
         }
         if (!ok) {
@@ -238,12 +250,12 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         const int quarter = warp & 3;                 // TMEM lane quarter this warp may access
         const int m = quarter * 32 + lane;            // accumulator row = (group, column)
         const int et = threadIdx.x - 64;              // 0..127
-        uint32_t uses[2] = {0u, 0u};   // same slot-claim sequence as the MMA issuer
+        uint32_t use0 = 0u, use1 = 0u;   // same slot-claim sequence as the MMA issuer
         uint32_t next_slot = 0;
         for (long long t = blockIdx.x; t < dl.total_tiles; t += gridDim.x) {
             const DirectProblemDev* P = direct_find(dl, t);
             const TileCoord tc = direct_tile(P, t);
-            const int J = P->J, G = P->G, rows_n = P->rows_n, Lpad = P->Lpad, T = P->T;
+            const int J = P->J, G = P->G, rows_n = P->rows_n, Lpad = P->Lpad, T = (TT == 0) ? P->T : TT;
             const int g = m / J;
             const int* gw = P->meta + (P->n_pass + 1);
             bool failed = false;
@@ -251,8 +263,9 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 const uint32_t s0 = (T == 2) ? 0u : next_slot;
                 next_slot = (T == 2) ? 0u : (next_slot ^ 1u);
                 bool ok = true;
-                for (int tt = 0; tt < T; ++tt)
-                    ok = ok && mbar_wait(smem_u32(&tail->tfull[s0 + tt]), uses[s0 + tt] & 1u, abort_flag, dl.err);
+                if (T == 2 || s0 == 0u) ok = mbar_wait(smem_u32(&tail->tfull[0]), use0 & 1u, abort_flag, dl.err);
+                if (ok && (T == 2 || s0 == 1u))
+                    ok = mbar_wait(smem_u32(&tail->tfull[1]), use1 & 1u, abort_flag, dl.err);
                 if (epi_any_failed(!ok)) { failed = true; break; }
                 tc_fence_after();
                 const int wg = (g < G) ? gw[p * 8 + g] : 0;
@@ -320,7 +333,8 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                     }
                     epi_bar();
                 }
-                for (int tt = 0; tt < T; ++tt) ++uses[s0 + tt];
+                if (T == 2 || s0 == 0u) ++use0;
+                if (T == 2 || s0 == 1u) ++use1;
             }
             if (failed) break;
         }
@@ -531,17 +545,22 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
     d->tiles = p.tiles;
 }
 
-int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st) {
+int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_T) {
     if (dl.total_tiles <= 0) return MORPH_OK;
     static int configured_device = -1;
     const int smem = direct_smem_bytes(kStages);
     if (configured_device != ctx->device) {
-        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         configured_device = ctx->device;
     }
+    const int T = dl.many == nullptr ? dl.single.T : uniform_T;
     long long grid = dl.total_tiles < ctx->num_sms ? dl.total_tiles : ctx->num_sms;
     prof_begin(ctx, st, "k_direct_fp8");
-    k_direct_fp8<<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
+    if (T == 1) k_direct_fp8<1><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
+    else if (T == 2) k_direct_fp8<2><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
+    else k_direct_fp8<0><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
     prof_end(ctx, st);
     ctx->launches += 1;
     MORPH_CUDA_TRY(cudaGetLastError());
