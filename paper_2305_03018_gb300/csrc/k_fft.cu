@@ -3,25 +3,29 @@
 //
 // The umbra f_Um(x, v) = [f(x) = v] (Eq. 7) is one-hot along the grey axis,
 // so its DFT along that axis (length R = L + max b, the number of degrees) is
-// exactly a_k(x) = exp(-2 pi i k f(x) / R): the encoder writes it from a
-// table, no grey-axis transform is run.  Likewise the SE umbra (Eq. 8) gives
-// s_k(y) = exp(-2 pi i k b(y) / R) on B.  For each grey frequency
-// k = 0..floor(R/2) (the count polynomial is real, so k and R-k are
+// exactly a_k(x) = exp(-2 pi i k f(x) / Rf): the encoder writes it from a
+// table, no forward grey-axis transform is run.  Rf is the smallest
+// 2^a 3^b 5^c >= R; every degree lies in [0, R), so the length-Rf circular
+// convolution along the grey axis never wraps.  Likewise the SE umbra
+// (Eq. 8) gives s_k(y) = exp(-2 pi i k b(y) / Rf) on B.  For each grey
+// frequency k = 0..Rf/2 (the count polynomial is real, so k and Rf-k are
 // conjugate) the spatial full-mode convolution a_k (*) s_k runs as a 2-D FFT
 // convolution on overlap-save tiles: an output tile of To_y x To_x pixels
 // reads an input tile extended by the SE's reach, placed at buffer offset 0 of
 // an Ny x Nx torus with Ny >= To_y + kh - 1, Nx >= To_x + kw - 1 (no wrap-around
-// reaches an output).  Step 3 inverts the grey-axis DFT per pixel,
-//     C(x, d) = (1 / (R Nx Ny)) sum_k w_k Re(c_k(x) exp(2 pi i k d / R)),
-// rounds to the nearest integer and takes the highest d with C >= 1,
-// scanning d downward and stopping there.
+// reaches an output).  Step 3 inverts the grey-axis DFT of each pixel with a
+// length-Rf FFT (the Hermitian half extended), divides by Rf Nx Ny, rounds to
+// the nearest integer and takes the highest d with C >= 1.
 //
 // Kernels (per wave of tiles):
 //   k_fft_rows_fwd : encode a_k for one input row, FFT along x, for every k;
 //   k_fft_cols     : FFT along y of C columns, multiply by the SE spectrum,
 //                    inverse FFT along y, keep the output rows;
 //   k_fft_rows_inv : inverse FFT along x of one output row, keep the output columns;
-//   k_fft_scan     : grey-axis inverse DFT + rounding + top-degree scan.
+//   k_fft_scan     : grey-axis inverse by direct evaluation, downward from a
+//                    proven start degree, stopping at the top (short grey axes);
+//   k_fft_range    : grey-axis inverse FFT of a group of pixels + rounding +
+//                    top-degree scan (one warp per pixel, ballots over d).
 // The FFTs are mixed-radix (2, 3, 4, 5) Stockham transforms in shared memory
 // with twiddle tables computed in FP64 (sincospi) and rounded to the working
 // precision.
@@ -172,7 +176,9 @@ struct FftArgs {
     long long row_stride, batch_stride;
     int L, flip, erode;
     // method
-    int R, K;                 // degrees, grey frequencies (floor(R/2) + 1)
+    int R, K;                 // degrees, grey frequencies (Rf/2 + 1)
+    int Rf;                   // grey-axis DFT length (smooth, >= R)
+    FftAxis ar;               // its factorisation
     int To_y, To_x, Rin_y, Win_x;   // output tile, input tile (To + k - 1)
     int ry, rx;               // SE reach below / right: kh - 1 - oy, kw - 1 - ox
     int tiles_x, tiles_y;
@@ -181,7 +187,7 @@ struct FftArgs {
     FftAxis ax, ay;
     const void* tw_x;         // Nx twiddles exp(-2 pi i j / Nx)
     const void* tw_y;
-    const void* wr;           // R twiddles exp(+2 pi i m / R)
+    const void* wr;           // Rf twiddles exp(-2 pi i m / Rf)
     const void* S;            // SE spectrum [K][Ny][Nx]
     void* buf;                // [wave_tiles][K][Ny][Nx]
     int32_t* out;
@@ -190,6 +196,9 @@ struct FftArgs {
     int validate;
     unsigned int* err;
     int colgroup;             // columns per CTA in k_fft_cols
+    int pixgroup;             // pixels per CTA in k_fft_range
+    int* tilemax;             // [wave_tiles] largest grey level in each input tile (k_fft_scan start bound)
+    int maxb;                 // largest SE offset
 };
 
 __device__ __forceinline__ int fft_load_px(const void* src, int dtype, long long idx) {
@@ -236,11 +245,17 @@ __global__ void __launch_bounds__(256) k_fft_rows_fwd(const FftArgs a) {
     }
     if (bad) atomicOr(a.err, MORPH_DEVERR_RANGE);
     __syncthreads();
+    if (a.tilemax) {
+        int mx = -1;
+        for (int p = threadIdx.x; p < a.Win_x; p += blockDim.x) mx = max(mx, lev[p]);
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0 && mx >= 0) atomicMax(a.tilemax + tl, mx);
+    }
     cT* dst = static_cast<cT*>(a.buf);
     for (int k = 0; k < a.K; ++k) {
         for (int p = threadIdx.x; p < Nx; p += blockDim.x) {
             cT v = cx<cT>(0, 0);
-            if (p < a.Win_x && lev[p] >= 0) v = cconj(wr[(static_cast<long long>(k) * lev[p]) % a.R]);
+            if (p < a.Win_x && lev[p] >= 0) v = wr[(static_cast<long long>(k) * lev[p]) % a.Rf];
             b0[p] = v;
         }
         __syncthreads();
@@ -304,15 +319,21 @@ __global__ void __launch_bounds__(256) k_fft_rows_inv(const FftArgs a) {
     for (int p = threadIdx.x; p < a.To_x; p += blockDim.x) row[p] = cconj(res[p + a.rx]);
 }
 
+// Step 3 by direct evaluation, for grey axes short enough that a few
+// evaluations per pixel beat a transform: C(x, d) = (1 / (Rf Nx Ny))
+// sum_k w_k Re(c_k(x) exp(2 pi i k d / Rf)), evaluated for d downward from
+// min(R - 1, largest level in the input tile + max b) -- no tap can exceed
+// that, so C is exactly 0 above it -- and stopping at the first d with
+// rint(C) >= 1.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft_scan(const FftArgs a) {
     using cT = typename CxT<T>::type;
-    const int Nx = a.ax.N, Ny = a.ay.N;
+    const int Nx = a.ax.N, Ny = a.ay.N, Rf = a.Rf;
     const long long per_tile = static_cast<long long>(a.To_y) * a.To_x;
     const long long total = per_tile * a.wave_tiles;
-    const cT* wr = static_cast<const cT*>(a.wr);
-    const T scale = static_cast<T>(1.0) / (static_cast<T>(a.R) * static_cast<T>(Nx) * static_cast<T>(Ny));
-    const bool nyq = (a.R % 2) == 0;
+    const cT* tw = static_cast<const cT*>(a.wr);     // exp(-2 pi i m / Rf): conjugate for the inverse
+    const T scale = static_cast<T>(1.0) / (static_cast<T>(Rf) * static_cast<T>(Nx) * static_cast<T>(Ny));
+    const bool nyq = (Rf % 2) == 0;
     float emax = 0.f;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -325,22 +346,23 @@ __global__ void __launch_bounds__(256) k_fft_scan(const FftArgs a) {
         if (i >= a.h || j >= a.w) continue;
         const cT* base = static_cast<const cT*>(a.buf) + (static_cast<long long>(tl) * a.K * Ny + q) * Nx + xo;
         const long long kstride = static_cast<long long>(Ny) * Nx;
+        int dstart = a.R - 1;
+        if (a.tilemax) dstart = min(dstart, a.tilemax[tl] + a.maxb);
         int D = -1, cnt = 0;
-        for (int d = a.R - 1; d >= 0; --d) {
+        for (int d = a.validate ? a.R - 1 : dstart; d >= 0; --d) {
             T s = base[0].x;
             int m = 0;
             for (int k = 1; k < a.K; ++k) {
                 m += d;
-                if (m >= a.R) m -= a.R;
+                if (m >= Rf) m -= Rf;
                 const cT c = base[k * kstride];
-                const cT w = wr[m];
-                const T re = c.x * w.x - c.y * w.y;
+                const cT w = tw[m];
+                const T re = c.x * w.x + c.y * w.y;       // Re(c * conj(w))
                 s += (nyq && k == a.K - 1) ? re : static_cast<T>(2) * re;
             }
             const T C = s * scale;
             const T rc = rint(C);
-            const float e = static_cast<float>(fabs(C - rc));
-            emax = fmaxf(emax, e);
+            emax = fmaxf(emax, static_cast<float>(fabs(C - rc)));
             if (rc >= static_cast<T>(1) && D < 0) {
                 D = d;
                 cnt = static_cast<int>(rc);
@@ -355,6 +377,78 @@ __global__ void __launch_bounds__(256) k_fft_scan(const FftArgs a) {
     if (a.count_err) {
         for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
         if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(a.count_err), __float_as_int(emax));
+    }
+}
+
+// Grey-axis inverse FFT + Step 3 for `pixgroup` consecutive output pixels of
+// one tile row: C(x, d) = (1 / (Rf Nx Ny)) sum_k c_k(x) exp(2 pi i k d / Rf)
+// with c_{Rf-k} = conj(c_k); then each warp scans its pixels' degrees from
+// R - 1 downward in chunks of 32 (ballot), keeping the top d with
+// rint(C) >= 1 and its count.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_range(const FftArgs a) {
+    using cT = typename CxT<T>::type;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Rf = a.ar.N, C = a.pixgroup, Nx = a.ax.N, Ny = a.ay.N;
+    cT* tw = reinterpret_cast<cT*>(sm);
+    cT* b0 = tw + Rf;
+    cT* b1 = b0 + Rf * C;
+    const cT* gtw = static_cast<const cT*>(a.wr);
+    const int x0 = blockIdx.x * C, q = blockIdx.y, tl = blockIdx.z;
+    int n, y0, tx0;
+    tile_origin(a, a.tile0 + tl, &n, &y0, &tx0);
+    for (int j = threadIdx.x; j < Rf; j += blockDim.x) tw[j] = gtw[j];
+    const cT* base = static_cast<const cT*>(a.buf) + (static_cast<long long>(tl) * a.K * Ny + q) * Nx;
+    const long long kstride = static_cast<long long>(Ny) * Nx;
+    // Hermitian extension, conjugated for the inverse transform
+    for (int t = threadIdx.x; t < Rf * C; t += blockDim.x) {
+        const int c = t % C, k = t / C;
+        const int xo = x0 + c;
+        cT v = cx<cT>(0, 0);
+        if (xo < a.To_x) {
+            if (k < a.K) v = cconj(base[k * kstride + xo]);
+            else v = base[(Rf - k) * kstride + xo];
+        }
+        b0[t] = v;
+    }
+    __syncthreads();
+    const cT* res = fft_block<T, cT>(b0, b1, a.ar, tw, C);
+    const T scale = static_cast<T>(1.0) / (static_cast<T>(Rf) * static_cast<T>(Nx) * static_cast<T>(Ny));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    float emax = 0.f;
+    for (int c = warp; c < C; c += nwarps) {
+        const int xo = x0 + c;
+        const int i = y0 + q, j = tx0 + xo;
+        if (xo >= a.To_x || i >= a.h || j >= a.w) continue;          // warp-uniform
+        int D = -1, cnt = 0;
+        for (int d0 = ((a.R - 1) / 32) * 32; d0 >= 0; d0 -= 32) {
+            const int d = d0 + lane;
+            T Cv = 0;
+            bool hit = false;
+            if (d < a.R) {
+                Cv = res[d * C + c].x * scale;          // real part of the conjugated result
+                const T rc = rint(Cv);
+                if (a.validate || D < 0) emax = fmaxf(emax, static_cast<float>(fabs(Cv - rc)));
+                hit = rc >= static_cast<T>(1);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (D < 0 && m) {
+                const int top = 31 - __clz(m);
+                D = d0 + top;
+                cnt = static_cast<int>(rint(__shfl_sync(0xffffffffu, static_cast<double>(Cv), top)));
+                if (!a.validate) break;
+            }
+        }
+        if (lane == 0) {
+            const int dval = D < 0 ? 0 : D;
+            const long long o = (static_cast<long long>(n) * a.h + i) * a.w + j;
+            a.out[o] = a.erode ? (a.L - 1 - dval) : dval;
+            if (a.out_cnt) a.out_cnt[o] = D < 0 ? 0 : cnt;
+        }
+    }
+    if (a.count_err) {
+        for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        if (lane == 0) atomicMax(reinterpret_cast<int*>(a.count_err), __float_as_int(emax));
     }
 }
 
@@ -466,17 +560,23 @@ static int smooth_at_least(int n) {
 // radix 3 and 5, the twiddle's own rounding and the complex multiply.
 static double stage_eta(int r, double u) { return (r + 4) * u; }
 
-double fft_error_bound(const FftAxis& ax, const FftAxis& ay, double sqrtP, int taps, int K, double u) {
+double fft_error_bound(const FftAxis& ax, const FftAxis& ay, const FftAxis& ar, double sqrtP, int taps, double u) {
     double e1 = 0.0;
     for (int s = 0; s < ax.nst; ++s) e1 += stage_eta(ax.rad[s], u);
     for (int s = 0; s < ay.nst; ++s) e1 += stage_eta(ay.rad[s], u);
-    // forward + inverse 2-D transforms, product and SE-spectrum rounding, input table rounding
+    // forward + inverse 2-D transforms, product and SE-spectrum rounding, input table rounding;
+    // the grey-axis inverse averages the frequencies' errors (weights summing to 1)
     const double conv = 1.01 * (2.0 * e1 + 4.0 * u) * sqrtP * static_cast<double>(taps);
-    // grey-axis inverse: K-term sum of values bounded by |B|, table rounding
-    const double range = (K + 4) * u * static_cast<double>(taps);
+    // grey-axis inverse FFT of a vector of counts whose 2-norm is at most |B|
+    double er = 0.0;
+    for (int s = 0; s < ar.nst; ++s) er += stage_eta(ar.rad[s], u);
+    const double range = 1.01 * (er + 4.0 * u) * static_cast<double>(taps);
     return conv + range;
 }
 
+}  // namespace morph
+
+namespace morph {
 
 FftPlan::~FftPlan() {
     for (void* q : {tw_x, tw_y, wr, S})
@@ -506,7 +606,9 @@ int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unpr
     p->prec = prec;
     p->taps = taps;
     p->R = f->L + maxb;
-    p->K = p->R / 2 + 1;
+    p->Rf = smooth_at_least(p->R);
+    if (p->Rf > kFftMaxN || !factor_axis(p->Rf, &p->ar)) return MORPH_E_UNSUPPORTED;
+    p->K = p->Rf / 2 + 1;
     p->ry = kh - 1 - se->oy;
     p->rx = kw - 1 - se->ox;
     p->kh = kh;
@@ -530,7 +632,7 @@ int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unpr
             if (!factor_axis(Nx, &ax)) continue;
             const double sqrtP = std::sqrt(static_cast<double>(std::min(To_y + kh - 1, f->h)) *
                                            static_cast<double>(std::min(To_x + kw - 1, f->w)));
-            const double bound = fft_error_bound(ax, ay, sqrtP, taps, p->K, u);
+            const double bound = fft_error_bound(ax, ay, p->ar, sqrtP, taps, u);
             if (!unproven && !(bound < 0.5)) continue;
             const double tiles = static_cast<double>(f->n) * nty * ntx;
             const double fl = tiles * p->K *
@@ -552,8 +654,11 @@ int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unpr
     p->Rin_y = p->To_y + kh - 1;
     p->Win_x = p->To_x + kw - 1;
     p->ntiles = static_cast<long long>(f->n) * p->tiles_y * p->tiles_x;
-    p->flop = best + static_cast<double>(f->n) * f->h * f->w * 3.0 * p->K * 4.0;
+    p->flop = best + static_cast<double>(f->n) * f->h * f->w * axis_flop(p->ar);
     p->colgroup = prec == 4 ? 4 : 2;
+    // pixels per k_fft_range CTA: two Rf-point buffers per pixel within ~160 KB
+    p->pixgroup = static_cast<int>(std::min<size_t>(32, std::max<size_t>(1, (160u * 1024u) /
+                                                                                (2u * p->Rf * 2u * prec))));
     const size_t per_tile = static_cast<size_t>(p->K) * p->ax.N * p->ay.N * 2 * prec;
     const size_t budget = size_t(4) << 30;
     long long wt = static_cast<long long>(budget / std::max<size_t>(per_tile, 1));
@@ -562,6 +667,10 @@ int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unpr
     if (wt > 65535) wt = 65535;
     p->wave_tiles = static_cast<int>(wt);
     p->buf_bytes = per_tile * static_cast<size_t>(wt);
+    // grey-axis inverse: a transform once the axis is long (a downward scan may
+    // then evaluate many degrees per pixel); direct evaluation otherwise
+    p->range_fft = p->Rf >= 128;
+    p->ws_bytes = p->buf_bytes + (p->range_fft ? 0 : sizeof(int) * static_cast<size_t>(wt));
     return MORPH_OK;
 }
 
@@ -573,6 +682,7 @@ static int set_fft_smem(size_t rows, size_t cols) {
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_fft_range<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     (void)rows;
     (void)cols;
     done = true;
@@ -594,7 +704,7 @@ static int set_plane_smem() {
 int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int prec, bool unproven, FftPlan* p) {
     int rc = plan_fft_tiles(f, se, prec, unproven, p);
     if (rc) return rc;
-    const int Nx = p->ax.N, Ny = p->ay.N, K = p->K, R = p->R;
+    const int Nx = p->ax.N, Ny = p->ay.N, K = p->K, Rf = p->Rf;
     rc = set_plane_smem();
     if (rc) return rc;
     if (prec == 4) rc = set_fft_smem<float>(0, 0);
@@ -603,15 +713,15 @@ int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int
     const size_t cbytes = 2 * static_cast<size_t>(prec);
     MORPH_CUDA_TRY(cudaMalloc(&p->tw_x, Nx * cbytes));
     MORPH_CUDA_TRY(cudaMalloc(&p->tw_y, Ny * cbytes));
-    MORPH_CUDA_TRY(cudaMalloc(&p->wr, R * cbytes));
+    MORPH_CUDA_TRY(cudaMalloc(&p->wr, Rf * cbytes));
     if (prec == 4) {
         k_twiddles<float><<<(Nx + 255) / 256, 256>>>(static_cast<float2*>(p->tw_x), Nx, -1);
         k_twiddles<float><<<(Ny + 255) / 256, 256>>>(static_cast<float2*>(p->tw_y), Ny, -1);
-        k_twiddles<float><<<(R + 255) / 256, 256>>>(static_cast<float2*>(p->wr), R, +1);
+        k_twiddles<float><<<(Rf + 255) / 256, 256>>>(static_cast<float2*>(p->wr), Rf, -1);
     } else {
         k_twiddles<double><<<(Nx + 255) / 256, 256>>>(static_cast<double2*>(p->tw_x), Nx, -1);
         k_twiddles<double><<<(Ny + 255) / 256, 256>>>(static_cast<double2*>(p->tw_y), Ny, -1);
-        k_twiddles<double><<<(R + 255) / 256, 256>>>(static_cast<double2*>(p->wr), R, +1);
+        k_twiddles<double><<<(Rf + 255) / 256, 256>>>(static_cast<double2*>(p->wr), Rf, -1);
     }
     ctx->launches += 3;
     MORPH_CUDA_TRY(cudaGetLastError());
@@ -638,7 +748,7 @@ int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int
     {
         const long long n = static_cast<long long>(K) * static_cast<long long>(taps.size());
         const unsigned blocks = static_cast<unsigned>(std::min<long long>((n + 255) / 256, 4096));
-        k_se_scatter<<<blocks, 256>>>(s64, K, Ny, Nx, d_taps, static_cast<int>(taps.size()), R);
+        k_se_scatter<<<blocks, 256>>>(s64, K, Ny, Nx, d_taps, static_cast<int>(taps.size()), Rf);
     }
     k_plane_rows<<<dim3(Ny, K), 256, smem_rows(Nx, 8)>>>(s64, p->ax, tw64x, Ny);
     const int C64 = 2;
@@ -681,6 +791,11 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
     a.erode = erode;
     a.R = p.R;
     a.K = p.K;
+    a.Rf = p.Rf;
+    a.ar = p.ar;
+    a.pixgroup = p.pixgroup;
+    a.maxb = p.R - f->L;
+    a.tilemax = p.range_fft ? nullptr : reinterpret_cast<int*>(static_cast<unsigned char*>(buf) + p.buf_bytes);
     a.To_y = p.To_y;
     a.To_x = p.To_x;
     a.Rin_y = p.Rin_y;
@@ -706,6 +821,7 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
     for (long long t0 = 0; t0 < p.ntiles; t0 += p.wave_tiles) {
         a.tile0 = t0;
         a.wave_tiles = static_cast<int>(std::min<long long>(p.wave_tiles, p.ntiles - t0));
+        if (a.tilemax) MORPH_CUDA_TRY(cudaMemsetAsync(a.tilemax, 0xff, sizeof(int) * a.wave_tiles, st));
         const size_t sr = smem_rows(p.ax.N, prec) + 4 * static_cast<size_t>(p.Win_x);
         prof_begin(ctx, st, prec == 4 ? "k_fft_rows_fwd<f32>" : "k_fft_rows_fwd<f64>");
         k_fft_rows_fwd<T><<<dim3(p.Rin_y, a.wave_tiles), 256, sr, st>>>(a);
@@ -717,11 +833,18 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
         prof_begin(ctx, st, prec == 4 ? "k_fft_rows_inv<f32>" : "k_fft_rows_inv<f64>");
         k_fft_rows_inv<T><<<dim3(p.To_y, p.K, a.wave_tiles), 256, smem_rows(p.ax.N, prec), st>>>(a);
         prof_end(ctx, st);
-        const long long px = static_cast<long long>(p.To_y) * p.To_x * a.wave_tiles;
-        const unsigned blocks = static_cast<unsigned>(std::min<long long>((px + 255) / 256, ctx->num_sms * 16LL));
-        prof_begin(ctx, st, prec == 4 ? "k_fft_scan<f32>" : "k_fft_scan<f64>");
-        k_fft_scan<T><<<blocks, 256, 0, st>>>(a);
-        prof_end(ctx, st);
+        if (p.range_fft) {
+            const size_t srange = static_cast<size_t>(p.Rf) * (1 + 2 * p.pixgroup) * 2 * prec;
+            prof_begin(ctx, st, prec == 4 ? "k_fft_range<f32>" : "k_fft_range<f64>");
+            k_fft_range<T><<<dim3((p.To_x + p.pixgroup - 1) / p.pixgroup, p.To_y, a.wave_tiles), 256, srange, st>>>(a);
+            prof_end(ctx, st);
+        } else {
+            const long long px = static_cast<long long>(p.To_y) * p.To_x * a.wave_tiles;
+            const unsigned blocks = static_cast<unsigned>(std::min<long long>((px + 255) / 256, ctx->num_sms * 16LL));
+            prof_begin(ctx, st, prec == 4 ? "k_fft_scan<f32>" : "k_fft_scan<f64>");
+            k_fft_scan<T><<<blocks, 256, 0, st>>>(a);
+            prof_end(ctx, st);
+        }
         ctx->launches += 4;
         MORPH_CUDA_TRY(cudaGetLastError());
     }
@@ -737,7 +860,7 @@ int launch_fft_in(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int er
 int launch_fft(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
                float* count_err, int validate, cudaStream_t st) {
     void* buf = nullptr;
-    int rc = ctx_workspace(ctx, p.buf_bytes, &buf);
+    int rc = ctx_workspace(ctx, p.ws_bytes, &buf);
     if (rc) return rc;
     if (count_err) MORPH_CUDA_TRY(cudaMemsetAsync(count_err, 0, sizeof(float), st));
     return launch_fft_in(ctx, p, f, erode, out, cnt, count_err, validate, buf, st);

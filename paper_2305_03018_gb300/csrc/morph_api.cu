@@ -410,7 +410,7 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         out->tile_w = q.To_x;
         out->tile_h = q.To_y;
         out->est_flop = q.flop;
-        out->workspace_bytes = q.buf_bytes;
+        out->workspace_bytes = q.ws_bytes;
     }
     return MORPH_OK;
 }

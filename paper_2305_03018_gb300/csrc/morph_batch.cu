@@ -89,7 +89,7 @@ int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts*
         off = align_up(off + planes_bytes(&b->items[i].f), 256);
     }
     size_t fft_need = 0;
-    for (int i : b->fft_items) fft_need = std::max(fft_need, b->items[i].plan->fft.buf_bytes);
+    for (int i : b->fft_items) fft_need = std::max(fft_need, b->items[i].plan->fft.ws_bytes);
     b->fft_off = off;
     off = align_up(off + fft_need, 256);
     b->total_bytes = std::max<size_t>(off, 256);

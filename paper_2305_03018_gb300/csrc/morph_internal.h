@@ -97,16 +97,19 @@ struct FftAxis {
 
 struct FftPlan {
     int prec = 8;                 // 4 = FP32, 8 = FP64
-    int taps = 0, R = 0, K = 0;   // |B|, degrees, grey frequencies
+    int taps = 0, R = 0, K = 0;   // |B|, degrees, grey frequencies (Rf/2 + 1)
+    int Rf = 0;                   // grey-axis DFT length: smallest 2^a 3^b 5^c >= R
     int kh = 0, kw = 0, ry = 0, rx = 0;
     int To_y = 0, To_x = 0, Rin_y = 0, Win_x = 0;
     int tiles_y = 0, tiles_x = 0;
     long long ntiles = 0;
-    int wave_tiles = 0, colgroup = 4;
-    size_t buf_bytes = 0;
+    int wave_tiles = 0, colgroup = 4, pixgroup = 16;
+    size_t buf_bytes = 0;         // spectra of one wave of tiles
+    size_t ws_bytes = 0;          // buf_bytes + per-tile scan bounds
+    bool range_fft = false;       // grey-axis inverse by FFT (long axes) or by direct evaluation
     double bound = 0;             // a-priori bound on |C - C_exact| for this precision
     double flop = 0;
-    FftAxis ax, ay;
+    FftAxis ax, ay, ar;
     void* tw_x = nullptr;
     void* tw_y = nullptr;
     void* wr = nullptr;
@@ -179,6 +182,6 @@ int launch_fft(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode
                float* count_err, int validate, cudaStream_t st);
 int launch_fft_in(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
                   float* count_err, int validate, void* buf, cudaStream_t st);
-double fft_error_bound(const FftAxis& ax, const FftAxis& ay, double sqrtP, int taps, int K, double u);
+double fft_error_bound(const FftAxis& ax, const FftAxis& ay, const FftAxis& ar, double sqrtP, int taps, double u);
 
 }  // namespace morph
