@@ -146,6 +146,21 @@ def _profile_traffic():
         return None, "summary without dram_bytes_per_launch"
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time (every rank must call it)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(px_per_rank_step: float, world: int, ms_per_step: float) -> float:
+    """Whole-job Mpix/s: every rank processes its own replica of the step."""
+    return world * px_per_rank_step / (ms_per_step * 1e-3) / 1e6
+
+
 # ------------------------------------------------------------- reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -250,11 +265,8 @@ def run_ours(args, ws, rank, local):
     kt = ctx.profile_read()
     clocks = clk.stop()
     ctx.check()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * px_per_step / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, dist, dev)
+    value = job_throughput(px_per_step, ws, ms)
 
     # ---- end to end through the C ABI: pinned host -> device -> ops -> host
     h2d = f_host.numel() * f_host.element_size()
@@ -272,11 +284,8 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = ws * px_per_step / (e2e_ms * 1e-3) / 1e6
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+    e2e = job_throughput(px_per_step, ws, e2e_ms)
 
     # ---- the same workload through the FFT forms of Step 2 (FP64 and FP32)
     forms = {"direct_fp8": {"value": value / ws, "ms_per_step": ms, "exact": True}}
