@@ -357,6 +357,7 @@ def _time_forms(ctx, probs, f_dev, L, ref_outs, px_per_step, stream, steps):
         exact = all(bool(torch.equal(o, r)) for o, r in zip(outs, ref_outs))
         worst = 0.0
         bounds = []
+        fft_flop = 0.0
         for p in probs:                          # measured max |C - rint C| over every degree
             err.zero_()
             o = torch.empty_like(ref_outs[0])
@@ -365,9 +366,11 @@ def _time_forms(ctx, probs, f_dev, L, ref_outs, px_per_step, stream, steps):
             worst = max(worst, float(err.item()))
             info = ctx.plan(f_dev, L, p.se, op=0 if p.op == "dilate" else 1, method=method, **kw)
             bounds.append(info.f32_bound if method == "fft_f32" else info.f64_bound)
+            fft_flop += info.est_flop
         ctx.check()
         res[name] = {"value": px_per_step / (ms * 1e-3) / 1e6, "ms_per_step": ms, "exact": exact,
                      "max_count_err": worst, "a_priori_bound_max": max(bounds),
+                     "fft_tflops_achieved": fft_flop / (ms * 1e-3) / 1e12,
                      "proven": max(bounds) < 0.5}
     return res
 
