@@ -141,6 +141,24 @@ int morph_dilate(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_
 int morph_erode(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_t *out,
                 int32_t *out_count, const morph_opts *opts, morph_stream_t stream);
 
+/* Composite operators (the combinations named in the paper's conclusion),
+ * computed exactly from the dilation and erosion above, with the same
+ * conventions (taps outside F skipped; int32, unclamped):
+ *   morph_open:     (f (-) b) (+) b   -- values in [-max b, L-1]
+ *   morph_close:    (f (+) b) (-) b   -- values in [0, L-1+max b]
+ *   morph_gradient: (f (+) b) - (f (-) b), the Beucher gradient
+ * The intermediate result is shifted into [0, L + max b) before the second
+ * operation, so opening and closing need L + max b <= 256
+ * (MORPH_E_UNSUPPORTED otherwise).  out: int32 [n][h][w] device.  The
+ * context keeps a device buffer of two int32 images for the intermediates
+ * (grown with a device synchronize). */
+int morph_open(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_t *out, const morph_opts *opts,
+               morph_stream_t stream);
+int morph_close(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_t *out, const morph_opts *opts,
+                morph_stream_t stream);
+int morph_gradient(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_t *out, const morph_opts *opts,
+                   morph_stream_t stream);
+
 /* Backward of the dilation for a learnable layer.  The upstream gradient
  * g = grad_out (fp32 [n][h][w], device) at x is routed to every tap attaining
  * the maximum, split equally among the cD(x) of them:

@@ -250,8 +250,8 @@ int prepare_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int
     return get_plan(ctx, f, &e.se, erode, route, plan, route == ROUTE_FFT32 && unproven);
 }
 
-static int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
-                   const morph_opts* opts, cudaStream_t st) {
+int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
+            const morph_opts* opts, cudaStream_t st) {
     if (!out) return inval("null output");
     std::shared_ptr<Plan> plan;
     int rc = prepare_problem(ctx, f, b, erode, opts, &plan);
@@ -340,6 +340,7 @@ int morph_ctx_destroy(morph_ctx* ctx) {
     }
     for (auto e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->ws2) cudaFree(ctx->ws2);
     if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;
     return MORPH_OK;

@@ -142,6 +142,8 @@ struct morph_ctx {
     unsigned int* d_err = nullptr;        // device error word
     void* ws = nullptr;                   // device workspace
     size_t ws_bytes = 0;
+    void* ws2 = nullptr;                  // intermediate images of composite operators
+    size_t ws2_bytes = 0;
     uint64_t launches = 0;
     std::unordered_map<std::string, std::shared_ptr<morph::Plan>> plans;
     std::unordered_map<std::string, std::shared_ptr<void>> aux_plans;   // backward tap lists, ...
@@ -176,6 +178,9 @@ int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, i
 int prepare_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, const morph_opts* opts,
                     std::shared_ptr<Plan>* plan);
 size_t planes_bytes(const morph_image* f);
+// one dilation (erode = 0) or erosion (erode = 1), the body of morph_dilate / morph_erode
+int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
+            const morph_opts* opts, cudaStream_t st);
 int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unproven, FftPlan* p);
 int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int prec, bool unproven, FftPlan* p);
 int launch_fft(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,

@@ -70,6 +70,12 @@ _SIGS = {
                                     ctypes.POINTER(morph_opts), _P]),
     "morph_erode": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P, _P,
                                    ctypes.POINTER(morph_opts), _P]),
+    "morph_open": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P,
+                                  ctypes.POINTER(morph_opts), _P]),
+    "morph_close": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P,
+                                   ctypes.POINTER(morph_opts), _P]),
+    "morph_gradient": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P,
+                                      ctypes.POINTER(morph_opts), _P]),
     "morph_dilate_backward": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P, _P, _P,
                                              _P, _P, _P]),
     "morph_run_batch": (ctypes.c_int, [_P, ctypes.POINTER(morph_problem), ctypes.c_int, ctypes.POINTER(morph_opts),
@@ -149,6 +155,21 @@ def morph_dilate(ctx, image, se, out_ptr, cnt_ptr, opts, stream) -> int:
 def morph_erode(ctx, image, se, out_ptr, cnt_ptr, opts, stream) -> int:
     return load_library().morph_erode(ctx, ctypes.byref(image), ctypes.byref(se), out_ptr, cnt_ptr,
                                       ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def morph_open(ctx, image, se, out_ptr, opts, stream) -> int:
+    return load_library().morph_open(ctx, ctypes.byref(image), ctypes.byref(se), out_ptr,
+                                     ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def morph_close(ctx, image, se, out_ptr, opts, stream) -> int:
+    return load_library().morph_close(ctx, ctypes.byref(image), ctypes.byref(se), out_ptr,
+                                      ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def morph_gradient(ctx, image, se, out_ptr, opts, stream) -> int:
+    return load_library().morph_gradient(ctx, ctypes.byref(image), ctypes.byref(se), out_ptr,
+                                         ctypes.byref(opts) if opts is not None else None, stream)
 
 
 def morph_dilate_backward(ctx, image, se, d_ptr, cd_ptr, g_ptr, gin_ptr, gse_ptr, stream) -> int:
@@ -319,6 +340,18 @@ class Context:
 
     def erode(self, f, L, se, method="auto", count=False, stream=None, **kw):
         return self._run(1, f, L, se, method, count, stream, **kw)
+
+    def composite(self, which, f, L, se, method="auto", stream=None, out=None):
+        """which: 'open' | 'close' | 'gradient'."""
+        import torch
+        img = make_image(f, L)
+        sv = se_view(se)
+        if out is None:
+            out = torch.empty((img.n, img.h, img.w), dtype=torch.int32, device=f.device)
+        fn = {"open": morph_open, "close": morph_close, "gradient": morph_gradient}[which]
+        st = stream if stream is not None else current_stream_handle(f.device)
+        check(fn(self.handle, img, sv.c, out.data_ptr(), make_opts(method), st), "morph_" + which)
+        return out
 
     def plan(self, f, L, se, op=0, method="auto", allow_unproven_f32=False, **_):
         img = make_image(f, L)
