@@ -47,7 +47,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FFT-form comparison")
     ap.add_argument("--cpu-rows", type=int, default=48, help="oracle sample: rows per operation")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5"], default="c2",
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "x1", "x2"], default="c2",
                     help="c2 (default) is the headline workload; the others time the remaining configurations")
     return ap.parse_args()
 
@@ -533,11 +533,64 @@ def run_config(args, ws, rank, local):
     return 0
 
 
+# ------------------------------------------------------ paper-shaped sweeps
+def run_sweep(args, ws, rank, local):
+    """The paper's runtime experiments on the GPU (Sec. 4.1): x1 = a 512x512
+    image with square full-support random filters 32^2..256^2; x2 = n x n
+    images with floor(n/10)^2 filters; values randint 0..15 (4-bit) and 0..255
+    (8-bit) for image and filter, as in the paper.  Seconds per dilation for
+    each exact form (forms agree bit for bit)."""
+    import numpy as np
+    import torch
+
+    from paper_2305_03018_gb300 import workloads as wl
+    from paper_2305_03018_gb300.morph import get_context
+    torch.cuda.set_device(local)
+    ctx = get_context(local)
+    if args.workload == "x1":
+        cases = [(512, k) for k in (32, 64, 128, 256)]
+    else:
+        cases = [(n, n // 10) for n in (128, 256, 512, 1024, 2048, 4096)]
+    rows = []
+    for bits, L in ((4, 16), (8, 256)):
+        for n, k in cases:
+            g = wl.rng(1000 * n + k + bits)
+            f = torch.from_numpy(wl.uniform_image(g, (1, n, n), L)).cuda()
+            se = wl.se_full_random(g, k, L - 1)
+            items = [(f, L, se, "dilate", None)]
+            forms, skipped = [], {}
+            for name, method in (("auto", "auto"), ("direct_fp8", "direct_fp8"), ("fft_f64", "fft_f64")):
+                est = ctx.plan(f, L, se, method=method)
+                rate = {1: 3.0e15, 2: 2.5e13, 3: 0.9e12}[est.method]
+                if est.est_flop / rate > 20.0:           # keep the sweep within minutes
+                    skipped[name] = f"skipped: estimated {est.est_flop / rate:.0f} s per op"
+                else:
+                    forms.append((name, method, {}))
+            res = _forms_table(ctx, items, forms, max(1, args.steps))
+            res.update({k: {"note": v} for k, v in skipped.items()})
+            info = ctx.plan(f, L, se, method="auto")
+            rows.append({"bits": bits, "image": n, "filter": k,
+                         "auto_method": {1: "direct_fp8", 2: "fft_f32", 3: "fft_f64"}.get(info.method),
+                         "s_per_op": {m: (r["ms_per_step"] * 1e-3 if r.get("ms_per_step") else None)
+                                      for m, r in res.items()},
+                         "exact_vs_first": all(r.get("exact_vs_first", False) for r in res.values()
+                                               if "note" not in r)})
+            del f
+            torch.cuda.empty_cache()
+    line = {"metric": METRIC, "workload": args.workload, "unit": "s per dilation", "steps": max(1, args.steps),
+            "data": "synthetic randint images and filters, as in the paper", "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     ws, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload in ("x1", "x2"):
+        return run_sweep(args, ws, rank, local)
     if args.workload != "c2":
         return run_config(args, ws, rank, local)
     return run_ours(args, ws, rank, local)

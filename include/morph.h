@@ -75,7 +75,7 @@ typedef struct {
 } morph_image;
 
 typedef struct {
-    int kh, kw;              /* box size, 1..63 each */
+    int kh, kw;              /* box size, 1..512 each (1..63 for morph_run_noalloc) */
     int oy, ox;              /* box entry of the spatial origin (any integers) */
     const uint8_t *mask;     /* host, kh*kw, row-major */
     const int32_t *offset;   /* host, kh*kw, >= 0 where mask != 0 */
@@ -166,6 +166,7 @@ int morph_gradient(morph_ctx *ctx, const morph_image *f, const morph_se *b, int3
  *   grad_se(y)  = sum_{x in F, x-y in F, f(x-y)+b(y) = D(x)} g(x) / cD(x),
  * the latter being the coefficient of t^b(y) in the lag-y cross-correlation
  * of g/cD * t^D with t^-f.  D and cD are the forward outputs (device int32).
+ * At most 65535 taps (MORPH_E_UNSUPPORTED beyond).
  * grad_in: nullable fp32 [n][h][w] device (overwritten).  grad_se: nullable
  * fp32 [kh][kw] device (overwritten; 0 outside B).  Deterministic: fixed
  * summation order, no atomics on floating point. */

@@ -133,7 +133,7 @@ extern "C" int morph_dilate_backward(morph_ctx* ctx, const morph_image* f, const
     if (f->dtype < MORPH_U8 || f->dtype > MORPH_I32 || f->n < 1 || f->h < 1 || f->w < 1) return MORPH_E_INVAL;
     if (f->row_stride < f->w || f->batch_stride < static_cast<int64_t>(f->h - 1) * f->row_stride + f->w)
         return MORPH_E_INVAL;
-    if (b->kh < 1 || b->kw < 1 || b->kh > 63 || b->kw > 63 || !b->mask || !b->offset) return MORPH_E_INVAL;
+    if (b->kh < 1 || b->kw < 1 || b->kh > 512 || b->kw > 512 || !b->mask || !b->offset) return MORPH_E_INVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     // tap list, cached per SE
     std::string key = "bwd|";
@@ -153,6 +153,7 @@ extern "C" int morph_dilate_backward(morph_ctx* ctx, const morph_image* f, const
                 if (b->offset[t] < 0) return MORPH_E_INVAL;
                 taps.push_back(BwdTap{r - b->oy, c - b->ox, b->offset[t], t});
             }
+        if (taps.size() > 65535) return MORPH_E_UNSUPPORTED;   // one grid row of partial sums per tap
         plan = std::make_shared<BwdPlan>();
         plan->ntaps = static_cast<int>(taps.size());
         if (plan->ntaps > 0) {

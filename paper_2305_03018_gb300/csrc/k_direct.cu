@@ -385,7 +385,8 @@ DirectPlan::~DirectPlan() {
     if (d_meta) cudaFree(d_meta);
 }
 
-int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, DirectPlan* p) {
+// Host part of the plan: tiles, groups, passes, metadata and the issued FLOP.
+int plan_direct_host(const morph_image* f, const morph_se* se, int erode, DirectPlan* p) {
     const int kh = se->kh, kw = se->kw;
     p->L = f->L;
     p->Lpad = 16;
@@ -472,6 +473,13 @@ int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, 
     p->issued_flop = static_cast<double>(p->tiles) * p->T * static_cast<double>(p->active_rows_total) * p->ksteps * 2.0 *
                      kDirectM * kDirectN * 32.0;
 
+    return MORPH_OK;
+}
+
+int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, DirectPlan* p) {
+    int rc0 = plan_direct_host(f, se, erode, p);
+    if (rc0 || p->taps == 0) return rc0;
+    const int kh = se->kh, kw = se->kw;
     // device copies and the Toeplitz blocks
     const size_t tb = static_cast<size_t>(p->toeplitz_blocks) * 128 * 128;
     MORPH_CUDA_TRY(cudaMalloc(&p->d_toeplitz, tb));

@@ -153,7 +153,7 @@ static int validate(const morph_image* f, const morph_se* b) {
     if (f->L < 2 || f->L > 256) return inval("L outside [2, 256]");
     if (f->row_stride < f->w) return inval("row_stride < w");
     if (f->batch_stride < static_cast<int64_t>(f->h - 1) * f->row_stride + f->w) return inval("batch_stride");
-    if (b->kh < 1 || b->kw < 1 || b->kh > 63 || b->kw > 63) return inval("SE box outside 1..63");
+    if (b->kh < 1 || b->kw < 1 || b->kh > 512 || b->kw > 512) return inval("SE box outside 1..512");
     if (!b->mask || !b->offset) return inval("null SE mask or offset");
     if (b->oy < -4096 || b->oy > 4096 || b->ox < -4096 || b->ox > 4096) return inval("SE origin");
     for (int t = 0; t < b->kh * b->kw; ++t)
@@ -204,10 +204,11 @@ size_t planes_bytes(const morph_image* f) {
     return static_cast<size_t>(f->n) * f->h * f->L * w_pad;
 }
 
-// Route for a request.  AUTO compares a time estimate of the FP8 direct route
-// (issued dense FLOP at the tensor rate the kernel reaches) with the FP32 FFT
-// route when that route's a-priori bound proves it exact; FP64 is never
-// chosen automatically (it is exact but slow on this part).
+// Route for a request.  AUTO estimates each exact route's time on the host
+// (no device work) and takes the fastest: the FP8 direct route (issued dense
+// FLOP at the tensor rate the kernel reaches), the FP32 FFT route when its
+// a-priori bound proves it exact, and the FP64 FFT route only where FP32 is
+// not provable (FP64 runs at 1/64 of FP32 on this part).
 static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, int method,
                         bool unproven, int* route) {
     if (method == MORPH_DIRECT_FP8) { *route = ROUTE_DIRECT; return MORPH_OK; }
@@ -217,17 +218,26 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
     const std::string key = "auto|" + plan_key(f, se, erode, 0);
     auto it = ctx->route_cache.find(key);
     if (it != ctx->route_cache.end()) { *route = it->second; return MORPH_OK; }
-    std::shared_ptr<Plan> dp;
-    int rc = get_plan(ctx, f, se, erode, ROUTE_DIRECT, &dp);
+    DirectPlan dp;
+    int rc = plan_direct_host(f, se, erode, &dp);
     if (rc) return rc;
     *route = ROUTE_DIRECT;
-    if (dp->route == ROUTE_DIRECT) {
-        const double t_direct = dp->direct.issued_flop / 2.0e15;
+    if (dp.taps > 0) {
+        double best = dp.issued_flop / 3.0e15;
         FftPlan fp;
+        const auto fft_time = [](const FftPlan& q, double flops_per_s) {
+            const double bytes = 5.0 * q.K * static_cast<double>(q.ax.N) * q.ay.N * 2.0 * q.prec * q.ntiles;
+            return q.flop / flops_per_s + bytes / 4.0e12;
+        };
         if (plan_fft_tiles(f, se, 4, false, &fp) == MORPH_OK) {
-            const double bytes = 5.0 * fp.K * static_cast<double>(fp.ax.N) * fp.ay.N * 8.0 * fp.ntiles;
-            const double t_fft = fp.flop / 2.5e13 + bytes / 4.0e12;
-            if (t_fft < t_direct) *route = ROUTE_FFT32;
+            const double t = fft_time(fp, 2.5e13);
+            if (t < best) { best = t; *route = ROUTE_FFT32; }
+        } else {
+            FftPlan f64;
+            if (plan_fft_tiles(f, se, 8, false, &f64) == MORPH_OK) {
+                const double t = fft_time(f64, 0.9e12);
+                if (t < best) { best = t; *route = ROUTE_FFT64; }
+            }
         }
     }
     (void)unproven;

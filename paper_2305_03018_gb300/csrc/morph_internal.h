@@ -167,6 +167,7 @@ int encode_tmap(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, co
 int launch_encode(morph_ctx* ctx, const EncodeJob* jobs, int njobs, long long total_items,
                   EncodeJob* d_jobs, cudaStream_t st);
 int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, DirectPlan* p);
+int plan_direct_host(const morph_image* f, const morph_se* se, int erode, DirectPlan* p);
 // uniform_T: tiles per unit shared by every problem of a batched launch (1 or 2), 0 if mixed
 int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_T = 0);
 int direct_smem_bytes(int stages);
