@@ -15,6 +15,10 @@ Every function computes the plain definition from the paper:
   duality, so that duality can be tested against it.
 * :func:`dilate_backward` -- the tie-split argmax gradient of the max-plus
   dilation, in fp64, summed in a fixed order.
+* :func:`erode_backward` -- the same for the erosion (argmin taps; b enters
+  with a minus sign).
+* :func:`dilate3d` / :func:`erode3d` -- the definitions on 3-D volumes with a
+  3-D SE (the method is stated for N-D images, Sec. 2.1 and Sec. 3).
 
 The arithmetic lives in ``morph_oracle.c`` (plain C, OpenMP over image rows
 only); :func:`build` compiles it with gcc.
@@ -65,8 +69,12 @@ def _load():
                                       i32p, i32p, ci, ci, ci]
             lib.orc_dilate_backward.argtypes = [i32p, ci, ci, ci, ci, ci, ci, ci, ci, u8p, i32p,
                                                 i32p, i32p, f64p, f64p, f64p]
+            lib.orc_erode_backward.argtypes = [i32p, ci, ci, ci, ci, ci, ci, ci, ci, u8p, i32p,
+                                               i32p, i32p, f64p, f64p, f64p]
+            lib.orc_morph3d.argtypes = [i32p, ci, ci, ci, ci, ci, ci, ci, ci, ci, ci, ci, u8p, i32p, ci,
+                                        i32p, i32p, ci]
             lib.orc_max_offset.argtypes = [ci, ci, u8p, i32p]
-            for fn in (lib.orc_dilate, lib.orc_erode, lib.orc_dilate_backward,
+            for fn in (lib.orc_dilate, lib.orc_erode, lib.orc_dilate_backward, lib.orc_erode_backward, lib.orc_morph3d,
                        lib.orc_max_offset, lib.orc_max_threads):
                 fn.restype = ctypes.c_int
             _lib = lib
@@ -165,6 +173,55 @@ def dilate_backward(f, L, mask, offset, origin, D, cD, g):
                                    _p(g, ctypes.c_double), _p(gf, ctypes.c_double),
                                    _p(gb, ctypes.c_double)))
     return gf, gb
+
+
+def erode_backward(f, L, mask, offset, origin, E, cE, g):
+    """Tie-split argmin gradient of the erosion; returns ``(grad_f, grad_b)`` in fp64."""
+    lib = _load()
+    f, mask, offset, oy, ox = _prep(f, mask, offset, origin)
+    N, H, W = f.shape
+    kh, kw = mask.shape
+    E = np.ascontiguousarray(np.asarray(E).reshape(N, H, W), dtype=np.int32)
+    cE = np.ascontiguousarray(np.asarray(cE).reshape(N, H, W), dtype=np.int32)
+    g = np.ascontiguousarray(np.asarray(g).reshape(N, H, W), dtype=np.float64)
+    gf = np.zeros((N, H, W), np.float64)
+    gb = np.zeros((kh, kw), np.float64)
+    _check(lib.orc_erode_backward(_p(f, ctypes.c_int32), N, H, W, int(L), kh, kw, oy, ox,
+                                  _p(mask, ctypes.c_uint8), _p(offset, ctypes.c_int32),
+                                  _p(E, ctypes.c_int32), _p(cE, ctypes.c_int32),
+                                  _p(g, ctypes.c_double), _p(gf, ctypes.c_double),
+                                  _p(gb, ctypes.c_double)))
+    return gf, gb
+
+
+def _morph3d(f, L, mask, offset, origin, op, nthreads):
+    lib = _load()
+    f = np.ascontiguousarray(np.asarray(f), dtype=np.int32)
+    if f.ndim == 3:
+        f = f[None]
+    mask = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+    offset = np.ascontiguousarray(np.asarray(offset), dtype=np.int32)
+    if f.ndim != 4 or mask.ndim != 3 or offset.shape != mask.shape:
+        raise ValueError("volume [N, Z, H, W] or [Z, H, W]; mask and offset [kd, kh, kw]")
+    N, Z, H, W = f.shape
+    kd, kh, kw = mask.shape
+    out = np.zeros(f.shape, np.int32)
+    cnt = np.zeros(f.shape, np.int32)
+    _check(lib.orc_morph3d(_p(f, ctypes.c_int32), N, Z, H, W, int(L), kd, kh, kw,
+                           int(origin[0]), int(origin[1]), int(origin[2]),
+                           _p(mask, ctypes.c_uint8), _p(offset, ctypes.c_int32), int(op),
+                           _p(out, ctypes.c_int32), _p(cnt, ctypes.c_int32), int(nthreads)))
+    return out, cnt
+
+
+def dilate3d(f, L, mask, offset, origin, nthreads=1):
+    """3-D dilation (Eq. 6new / Eq. 6 on volumes); returns ``(D, cD)``."""
+    return _morph3d(f, L, mask, offset, origin, 0, nthreads)
+
+
+def erode3d(f, L, mask, offset, origin, nthreads=1):
+    """3-D erosion (Eq. Erosion on volumes); returns ``(E, cE)``."""
+    return _morph3d(f, L, mask, offset, origin, 1, nthreads)
 
 
 def max_threads() -> int:

@@ -231,6 +231,117 @@ int orc_dilate_backward(const int32_t *f, int N, int H, int W, int L,
     return ORC_OK;
 }
 
+/*
+ * Backward pass of erosion (Eq. Erosion): g(x) goes to every tap attaining
+ * the minimum at x, split equally among the cE(x) such taps; b enters with a
+ * minus sign.  In fp64, summed in a fixed order:
+ *   grad_f(p) = sum over y in B (row-major box order) with p - y in F and
+ *               f(p) - b(y) = E(p - y) of g(p - y) / cE(p - y);
+ *   grad_b(y) = - sum over x in F (image-major, row-major) with x + y in F and
+ *               f(x + y) - b(y) = E(x) of g(x) / cE(x);  0 for y not in B.
+ */
+int orc_erode_backward(const int32_t *f, int N, int H, int W, int L,
+                       int kh, int kw, int oy, int ox,
+                       const uint8_t *mask, const int32_t *off,
+                       const int32_t *E, const int32_t *cE, const double *g,
+                       double *grad_f, double *grad_b)
+{
+    int rc = check_args(N, H, W, L, kh, kw, oy, ox, mask, off);
+    if (rc) return rc;
+    rc = check_image(f, (int64_t)N * H * W, L);
+    if (rc) return rc;
+    if (grad_f) {
+        for (int n = 0; n < N; ++n)
+            for (int i = 0; i < H; ++i)
+                for (int j = 0; j < W; ++j) {
+                    const int64_t p = ((int64_t)n * H + i) * W + j;
+                    double acc = 0.0;
+                    for (int r = 0; r < kh; ++r)
+                        for (int c = 0; c < kw; ++c) {
+                            if (!mask[r * kw + c]) continue;
+                            const int ti = i - (r - oy), tj = j - (c - ox);
+                            if (ti < 0 || ti >= H || tj < 0 || tj >= W) continue;
+                            const int64_t x = ((int64_t)n * H + ti) * W + tj;
+                            if (f[p] - off[r * kw + c] == E[x] && cE[x] > 0)
+                                acc += g[x] / (double)cE[x];
+                        }
+                    grad_f[p] = acc;
+                }
+    }
+    if (grad_b) {
+        for (int r = 0; r < kh; ++r)
+            for (int c = 0; c < kw; ++c) {
+                double acc = 0.0;
+                if (mask[r * kw + c]) {
+                    for (int n = 0; n < N; ++n)
+                        for (int i = 0; i < H; ++i)
+                            for (int j = 0; j < W; ++j) {
+                                const int si = i + (r - oy), sj = j + (c - ox);
+                                if (si < 0 || si >= H || sj < 0 || sj >= W) continue;
+                                const int64_t x = ((int64_t)n * H + i) * W + j;
+                                const int64_t s = ((int64_t)n * H + si) * W + sj;
+                                if (f[s] - off[r * kw + c] == E[x] && cE[x] > 0)
+                                    acc += g[x] / (double)cE[x];
+                            }
+                }
+                grad_b[r * kw + c] = -acc;
+            }
+    }
+    return ORC_OK;
+}
+
+/*
+ * 3-D volumes (the method is stated for N-D images, Sec. 2.1 and Sec. 3):
+ * f on [0,Z) x [0,H) x [0,W) per volume, N volumes; SE on a kd x kh x kw box
+ * with origin (oz, oy, ox), box entry (q, r, c) = offset (q-oz, r-oy, c-ox).
+ *   op = 0: dilation  max{ f(x - y) + b(y) : x - y in F, y in B }, 0 if none;
+ *   op = 1: erosion   min{ f(x + y) - b(y) : x + y in F, y in B }, L-1 if none;
+ * out_c = number of taps attaining it (0 if none).
+ */
+int orc_morph3d(const int32_t *f, int N, int Z, int H, int W, int L,
+                int kd, int kh, int kw, int oz, int oy, int ox,
+                const uint8_t *mask, const int32_t *off, int op,
+                int32_t *out, int32_t *out_c, int nthreads)
+{
+    if (N < 0 || Z < 0 || H < 0 || W < 0 || L < 1 || kd < 1 || kh < 1 || kw < 1) return ORC_EINVAL;
+    for (int t = 0; t < kd * kh * kw; ++t)
+        if (mask[t] && off[t] < 0) return ORC_ERANGE;
+    if (check_image(f, (int64_t)N * Z * H * W, L)) return ORC_ERANGE;
+    const int sgn = op ? 1 : -1;   /* source = x + sgn * y */
+    const int64_t nrows = (int64_t)N * Z * H;
+    (void)nthreads;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t q0 = 0; q0 < nrows; ++q0) {
+        const int n = (int)(q0 / ((int64_t)Z * H));
+        const int z = (int)((q0 / H) % Z);
+        const int i = (int)(q0 % H);
+        const int32_t *fn = f + (int64_t)n * Z * H * W;
+        for (int j = 0; j < W; ++j) {
+            int have = 0, best = 0, nbest = 0;
+            for (int q = 0; q < kd; ++q)
+                for (int r = 0; r < kh; ++r)
+                    for (int c = 0; c < kw; ++c) {
+                        const int t = (q * kh + r) * kw + c;
+                        if (!mask[t]) continue;
+                        const int sz = z + sgn * (q - oz), si = i + sgn * (r - oy), sj = j + sgn * (c - ox);
+                        if (sz < 0 || sz >= Z || si < 0 || si >= H || sj < 0 || sj >= W) continue;
+                        const int v = fn[((int64_t)sz * H + si) * W + sj];
+                        const int s = op ? v - off[t] : v + off[t];
+                        const int better = op ? (s < best) : (s > best);
+                        if (!have || better) { best = s; nbest = 1; have = 1; }
+                        else if (s == best) nbest += 1;
+                    }
+            const int64_t px = ((int64_t)(n * (int64_t)Z + z) * H + i) * W + j;
+            out[px] = have ? best : (op ? L - 1 : 0);
+            out_c[px] = have ? nbest : 0;
+        }
+    }
+    return ORC_OK;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int orc_max_threads(void)
 {
