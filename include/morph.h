@@ -141,6 +141,35 @@ int morph_dilate(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_
 int morph_erode(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_t *out,
                 int32_t *out_count, const morph_opts *opts, morph_stream_t stream);
 
+/* 3-D volumes (the method is stated for N-D images, Sec. 2.1 and Sec. 3). */
+typedef struct {
+    const void *data;        /* device pointer to voxel (0,0,0) of volume 0 */
+    int dtype;               /* enum morph_dtype */
+    int n, d, h, w;          /* volumes, slices, rows, columns (each >= 1) */
+    int64_t row_stride;      /* elements between rows */
+    int64_t slice_stride;    /* elements between slices */
+    int64_t volume_stride;   /* elements between volumes */
+    int L;                   /* grey levels, 2 <= L <= 256 */
+} morph_volume;
+
+typedef struct {
+    int kd, kh, kw;          /* box size; kd 1..512, kh and kw as morph_se */
+    int oz, oy, ox;          /* box entry of the origin */
+    const uint8_t *mask;     /* host, kd*kh*kw, slice-major then row-major */
+    const int32_t *offset;   /* host, kd*kh*kw, >= 0 where mask != 0 */
+} morph_se3d;
+
+/* 3-D dilation / erosion with the conventions of the 2-D calls (taps outside
+ * the volume skipped; 0 resp. L-1 where no tap is valid; int32, unclamped).
+ * out and nullable out_count: int32 [n][d][h][w] device, contiguous.  Each SE
+ * slice runs through the 2-D routes over all slices of a volume; the
+ * per-slice results are folded by max (min) with counts summed at ties.
+ * Uses the context's second workspace (three int32 volumes). */
+int morph_dilate3d(morph_ctx *ctx, const morph_volume *f, const morph_se3d *b, int32_t *out,
+                   int32_t *out_count, const morph_opts *opts, morph_stream_t stream);
+int morph_erode3d(morph_ctx *ctx, const morph_volume *f, const morph_se3d *b, int32_t *out,
+                  int32_t *out_count, const morph_opts *opts, morph_stream_t stream);
+
 /* Composite operators (the combinations named in the paper's conclusion),
  * computed exactly from the dilation and erosion above, with the same
  * conventions (taps outside F skipped; int32, unclamped):
@@ -173,6 +202,15 @@ int morph_gradient(morph_ctx *ctx, const morph_image *f, const morph_se *b, int3
 int morph_dilate_backward(morph_ctx *ctx, const morph_image *f, const morph_se *b,
                           const int32_t *D, const int32_t *cD, const float *grad_out,
                           float *grad_in, float *grad_se, morph_stream_t stream);
+
+/* Backward of the erosion: g(x) goes to every tap attaining the minimum,
+ * split equally among the cE(x) of them, and b enters with a minus sign:
+ *   grad_in(p)  =   sum_{y in B, p-y in F, f(p)-b(y) = E(p-y)} g(p-y) / cE(p-y)
+ *   grad_se(y)  = - sum_{x in F, x+y in F, f(x+y)-b(y) = E(x)} g(x) / cE(x).
+ * E and cE are morph_erode's outputs; other arguments as morph_dilate_backward. */
+int morph_erode_backward(morph_ctx *ctx, const morph_image *f, const morph_se *b,
+                         const int32_t *E, const int32_t *cE, const float *grad_out,
+                         float *grad_in, float *grad_se, morph_stream_t stream);
 
 /* One problem of a heterogeneous batch. */
 typedef struct {

@@ -1,4 +1,5 @@
-// Backward of the dilation for a learnable morphological layer.
+// Backward of the dilation (and of the erosion) for a learnable
+// morphological layer.
 //
 // The forward value at x is the top degree D(x) of the count polynomial
 // (Step 3, Eq. 9) and its top coefficient cD(x) counts the SE taps attaining
@@ -9,6 +10,10 @@
 // sum_x (g / cD)(x) t^D(x) t^-f(x - y); the kernel evaluates that single
 // coefficient.  Both sums run in a fixed order (taps in box order; pixels in
 // fixed chunks reduced by a fixed tree), so results are deterministic.
+// Erosion (Eq. Erosion, E(x) = min f(x + y) - b(y), count cE) is the same
+// with the tap direction and the sign of b reversed (sgn = -1):
+//   grad_in(p)  = sum_{y, p - y in F, f(p) - b(y) = E(p - y)} g(p - y) / cE(p - y)
+//   grad_se(y)  = - sum_{x, x + y in F, f(x + y) - b(y) = E(x)} g(x) / cE(x)
 #include "morph_internal.h"
 #include "ptx.cuh"
 
@@ -28,6 +33,7 @@ struct BwdImage {
     const void* f;
     int dtype, n, h, w;
     long long row_stride, batch_stride;
+    int sgn;        // +1 dilation, -1 erosion
 };
 
 __global__ void __launch_bounds__(256) k_bwd_input(BwdImage im, const int32_t* __restrict__ D,
@@ -45,10 +51,10 @@ __global__ void __launch_bounds__(256) k_bwd_input(BwdImage im, const int32_t* _
         float acc = 0.f;
         for (int t = 0; t < ntaps; ++t) {
             const BwdTap tp = taps[t];
-            const int xi = i + tp.dy, xj = j + tp.dx;
+            const int xi = i + im.sgn * tp.dy, xj = j + im.sgn * tp.dx;
             if (xi < 0 || xi >= im.h || xj < 0 || xj >= im.w) continue;
             const long long x = (static_cast<long long>(n) * im.h + xi) * im.w + xj;
-            if (fp + tp.b == D[x]) {
+            if (fp + im.sgn * tp.b == D[x]) {
                 const int c = cD[x];
                 if (c > 0) acc += g[x] / static_cast<float>(c);
             }
@@ -79,10 +85,10 @@ __global__ void __launch_bounds__(kSeThreads) k_bwd_se_partial(BwdImage im, cons
         const long long rr = x / im.w;
         const int i = static_cast<int>(rr % im.h);
         const int n = static_cast<int>(rr / im.h);
-        const int si = i - tp.dy, sj = j - tp.dx;
+        const int si = i - im.sgn * tp.dy, sj = j - im.sgn * tp.dx;
         if (si < 0 || si >= im.h || sj < 0 || sj >= im.w) continue;
         const int fs = load_px(im.f, im.dtype, n * im.batch_stride + si * im.row_stride + sj);
-        if (fs + tp.b == D[x]) {
+        if (fs + im.sgn * tp.b == D[x]) {
             const int c = cD[x];
             if (c > 0) acc += g[x] / static_cast<float>(c);
         }
@@ -100,13 +106,13 @@ __global__ void __launch_bounds__(kSeThreads) k_bwd_se_partial(BwdImage im, cons
 
 // grad_se[box] = sum of the partials of its tap in chunk order (fp64 accumulator); 0 off B.
 __global__ void k_bwd_se_final(const float* __restrict__ partial, int nchunks, const BwdTap* __restrict__ taps,
-                               int ntaps, int nbox, float* __restrict__ grad_se) {
+                               int ntaps, int nbox, int sgn, float* __restrict__ grad_se) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) grad_se[b] = 0.f;
     __syncthreads();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntaps; t += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int c = 0; c < nchunks; ++c) s += partial[static_cast<long long>(t) * nchunks + c];
-        grad_se[taps[t].box] = static_cast<float>(s);
+        grad_se[taps[t].box] = static_cast<float>(sgn * s);
     }
 }
 
@@ -126,9 +132,9 @@ struct BwdPlan {
 
 }  // namespace morph
 
-extern "C" int morph_dilate_backward(morph_ctx* ctx, const morph_image* f, const morph_se* b, const int32_t* D,
-                                     const int32_t* cD, const float* grad_out, float* grad_in, float* grad_se,
-                                     morph_stream_t stream) {
+static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b, const int32_t* D,
+                         const int32_t* cD, const float* grad_out, float* grad_in, float* grad_se,
+                         morph_stream_t stream, int sgn) {
     if (!ctx || !f || !b || !f->data || !D || !cD || !grad_out) return MORPH_E_INVAL;
     if (f->dtype < MORPH_U8 || f->dtype > MORPH_I32 || f->n < 1 || f->h < 1 || f->w < 1) return MORPH_E_INVAL;
     if (f->row_stride < f->w || f->batch_stride < static_cast<int64_t>(f->h - 1) * f->row_stride + f->w)
@@ -163,7 +169,7 @@ extern "C" int morph_dilate_backward(morph_ctx* ctx, const morph_image* f, const
         }
         ctx->aux_plans.emplace(key, plan);
     }
-    BwdImage im{f->data, f->dtype, f->n, f->h, f->w, f->row_stride, f->batch_stride};
+    BwdImage im{f->data, f->dtype, f->n, f->h, f->w, f->row_stride, f->batch_stride, sgn};
     const long long total = static_cast<long long>(f->n) * f->h * f->w;
     if (grad_in) {
         long long blocks = (total + 255) / 256;
@@ -192,10 +198,22 @@ extern "C" int morph_dilate_backward(morph_ctx* ctx, const morph_image* f, const
             MORPH_CUDA_TRY(cudaGetLastError());
         }
         prof_begin(ctx, st, "k_bwd_se_final");
-        k_bwd_se_final<<<1, 1024, 0, st>>>(partial, nchunks, plan->d_taps, plan->ntaps, nbox, grad_se);
+        k_bwd_se_final<<<1, 1024, 0, st>>>(partial, nchunks, plan->d_taps, plan->ntaps, nbox, sgn, grad_se);
         prof_end(ctx, st);
         ctx->launches += 1;
         MORPH_CUDA_TRY(cudaGetLastError());
     }
     return MORPH_OK;
+}
+
+extern "C" int morph_dilate_backward(morph_ctx* ctx, const morph_image* f, const morph_se* b, const int32_t* D,
+                                     const int32_t* cD, const float* grad_out, float* grad_in, float* grad_se,
+                                     morph_stream_t stream) {
+    return backward_impl(ctx, f, b, D, cD, grad_out, grad_in, grad_se, stream, +1);
+}
+
+extern "C" int morph_erode_backward(morph_ctx* ctx, const morph_image* f, const morph_se* b, const int32_t* E,
+                                    const int32_t* cE, const float* grad_out, float* grad_in, float* grad_se,
+                                    morph_stream_t stream) {
+    return backward_impl(ctx, f, b, E, cE, grad_out, grad_in, grad_se, stream, -1);
 }

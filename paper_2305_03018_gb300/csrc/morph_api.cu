@@ -111,6 +111,22 @@ int ctx_workspace(morph_ctx* ctx, size_t bytes, void** out) {
     return MORPH_OK;
 }
 
+int ctx_workspace2(morph_ctx* ctx, size_t bytes, void** out) {
+    if (bytes > ctx->ws2_bytes) {
+        MORPH_CUDA_TRY(cudaDeviceSynchronize());
+        if (ctx->ws2) cudaFree(ctx->ws2);
+        ctx->ws2 = nullptr;
+        ctx->ws2_bytes = 0;
+        if (cudaMalloc(&ctx->ws2, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return MORPH_E_NOMEM;
+        }
+        ctx->ws2_bytes = bytes;
+    }
+    *out = ctx->ws2;
+    return MORPH_OK;
+}
+
 // ------------------------------------------------------------------ plans
 
 // SE after the erosion-by-duality reflection (Sec. 2.1): b_reflected(y) = b(-y),

@@ -38,21 +38,11 @@ static int add_const(morph_ctx* ctx, const int32_t* in, int32_t* out, long long 
     return MORPH_OK;
 }
 
-// Intermediate int32 images (count of them x pixels), grown with a device sync.
 static int ws2(morph_ctx* ctx, size_t bytes, int32_t** out) {
-    if (bytes > ctx->ws2_bytes) {
-        MORPH_CUDA_TRY(cudaDeviceSynchronize());
-        if (ctx->ws2) cudaFree(ctx->ws2);
-        ctx->ws2 = nullptr;
-        ctx->ws2_bytes = 0;
-        if (cudaMalloc(&ctx->ws2, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return MORPH_E_NOMEM;
-        }
-        ctx->ws2_bytes = bytes;
-    }
-    *out = static_cast<int32_t*>(ctx->ws2);
-    return MORPH_OK;
+    void* p = nullptr;
+    const int rc = ctx_workspace2(ctx, bytes, &p);
+    *out = static_cast<int32_t*>(p);
+    return rc;
 }
 
 static int max_offset(const morph_se* b) {

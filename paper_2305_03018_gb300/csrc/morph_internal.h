@@ -158,6 +158,8 @@ void prof_end(morph_ctx* ctx, cudaStream_t st);
 
 // Workspace of at least `bytes` (grows with a device synchronize).
 int ctx_workspace(morph_ctx* ctx, size_t bytes, void** out);
+// Second workspace for intermediate int32 images of composite and 3-D operators.
+int ctx_workspace2(morph_ctx* ctx, size_t bytes, void** out);
 
 // Encoding of tensor maps through the driver entry point.
 int encode_tmap(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, const uint64_t* dims,

@@ -38,6 +38,18 @@ class morph_se(ctypes.Structure):
                 ("mask", ctypes.POINTER(ctypes.c_uint8)), ("offset", ctypes.POINTER(ctypes.c_int32))]
 
 
+class morph_volume(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int), ("n", ctypes.c_int), ("d", ctypes.c_int),
+                ("h", ctypes.c_int), ("w", ctypes.c_int), ("row_stride", ctypes.c_int64),
+                ("slice_stride", ctypes.c_int64), ("volume_stride", ctypes.c_int64), ("L", ctypes.c_int)]
+
+
+class morph_se3d(ctypes.Structure):
+    _fields_ = [("kd", ctypes.c_int), ("kh", ctypes.c_int), ("kw", ctypes.c_int), ("oz", ctypes.c_int),
+                ("oy", ctypes.c_int), ("ox", ctypes.c_int), ("mask", ctypes.POINTER(ctypes.c_uint8)),
+                ("offset", ctypes.POINTER(ctypes.c_int32))]
+
+
 class morph_opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("flags", ctypes.c_int), ("count_err", ctypes.c_void_p)]
 
@@ -70,6 +82,10 @@ _SIGS = {
                                     ctypes.POINTER(morph_opts), _P]),
     "morph_erode": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P, _P,
                                    ctypes.POINTER(morph_opts), _P]),
+    "morph_dilate3d": (ctypes.c_int, [_P, ctypes.POINTER(morph_volume), ctypes.POINTER(morph_se3d), _P, _P,
+                                      ctypes.POINTER(morph_opts), _P]),
+    "morph_erode3d": (ctypes.c_int, [_P, ctypes.POINTER(morph_volume), ctypes.POINTER(morph_se3d), _P, _P,
+                                     ctypes.POINTER(morph_opts), _P]),
     "morph_open": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P,
                                   ctypes.POINTER(morph_opts), _P]),
     "morph_close": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P,
@@ -78,6 +94,8 @@ _SIGS = {
                                       ctypes.POINTER(morph_opts), _P]),
     "morph_dilate_backward": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P, _P, _P,
                                              _P, _P, _P]),
+    "morph_erode_backward": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P, _P, _P,
+                                            _P, _P, _P]),
     "morph_run_batch": (ctypes.c_int, [_P, ctypes.POINTER(morph_problem), ctypes.c_int, ctypes.POINTER(morph_opts),
                                        _P]),
     "morph_batch_capture": (ctypes.c_int, [_P, ctypes.POINTER(morph_problem), ctypes.c_int,
@@ -157,6 +175,16 @@ def morph_erode(ctx, image, se, out_ptr, cnt_ptr, opts, stream) -> int:
                                       ctypes.byref(opts) if opts is not None else None, stream)
 
 
+def morph_dilate3d(ctx, volume, se, out_ptr, cnt_ptr, opts, stream) -> int:
+    return load_library().morph_dilate3d(ctx, ctypes.byref(volume), ctypes.byref(se), out_ptr, cnt_ptr,
+                                         ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def morph_erode3d(ctx, volume, se, out_ptr, cnt_ptr, opts, stream) -> int:
+    return load_library().morph_erode3d(ctx, ctypes.byref(volume), ctypes.byref(se), out_ptr, cnt_ptr,
+                                        ctypes.byref(opts) if opts is not None else None, stream)
+
+
 def morph_open(ctx, image, se, out_ptr, opts, stream) -> int:
     return load_library().morph_open(ctx, ctypes.byref(image), ctypes.byref(se), out_ptr,
                                      ctypes.byref(opts) if opts is not None else None, stream)
@@ -175,6 +203,11 @@ def morph_gradient(ctx, image, se, out_ptr, opts, stream) -> int:
 def morph_dilate_backward(ctx, image, se, d_ptr, cd_ptr, g_ptr, gin_ptr, gse_ptr, stream) -> int:
     return load_library().morph_dilate_backward(ctx, ctypes.byref(image), ctypes.byref(se), d_ptr, cd_ptr, g_ptr,
                                                 gin_ptr, gse_ptr, stream)
+
+
+def morph_erode_backward(ctx, image, se, e_ptr, ce_ptr, g_ptr, gin_ptr, gse_ptr, stream) -> int:
+    return load_library().morph_erode_backward(ctx, ctypes.byref(image), ctypes.byref(se), e_ptr, ce_ptr, g_ptr,
+                                               gin_ptr, gse_ptr, stream)
 
 
 def morph_run_batch(ctx, problems, opts, stream) -> int:
@@ -259,6 +292,43 @@ def make_image(t, L: int) -> morph_image:
     return img
 
 
+def make_volume(t, L: int) -> morph_volume:
+    """C view of a CUDA integer tensor of shape [N, D, H, W] (or [D, H, W])."""
+    if t.dim() == 3:
+        t = t.unsqueeze(0)
+    if t.dim() != 4 or not t.is_cuda:
+        raise ValueError("volume must be a CUDA tensor [N, D, H, W] or [D, H, W]")
+    name = str(t.dtype).replace("torch.", "")
+    if name not in _DT:
+        raise ValueError(f"unsupported volume dtype {t.dtype}")
+    if t.stride(3) != 1:
+        raise ValueError("volume columns must be contiguous")
+    v = morph_volume()
+    v.data = t.data_ptr()
+    v.dtype = _DT[name]
+    v.n, v.d, v.h, v.w = (int(s) for s in t.shape)
+    v.row_stride = int(t.stride(2)) if v.h > 1 else v.w
+    v.slice_stride = int(t.stride(1)) if v.d > 1 else v.h * v.row_stride
+    v.volume_stride = int(t.stride(0)) if v.n > 1 else v.d * v.slice_stride
+    v.L = int(L)
+    return v
+
+
+class SE3DView:
+    """Host arrays of a 3-D SE kept alive next to the C struct."""
+
+    def __init__(self, mask, offset, origin):
+        self.mask = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        self.offset = np.ascontiguousarray(np.asarray(offset), dtype=np.int32)
+        if self.mask.ndim != 3 or self.offset.shape != self.mask.shape:
+            raise ValueError("mask and offset must be 3-D arrays of one shape")
+        self.c = morph_se3d()
+        self.c.kd, self.c.kh, self.c.kw = (int(s) for s in self.mask.shape)
+        self.c.oz, self.c.oy, self.c.ox = (int(o) for o in origin)
+        self.c.mask = self.mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        self.c.offset = self.offset.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
 class SEView:
     """Host arrays of an SE kept alive next to the C struct that points at them."""
 
@@ -340,6 +410,27 @@ class Context:
 
     def erode(self, f, L, se, method="auto", count=False, stream=None, **kw):
         return self._run(1, f, L, se, method, count, stream, **kw)
+
+    def _run3d(self, op, f, L, mask, offset, origin, method, count, stream):
+        import torch
+        vol = make_volume(f, L)
+        sv = SE3DView(mask, offset, origin)
+        shape = (vol.n, vol.d, vol.h, vol.w)
+        out = torch.empty(shape, dtype=torch.int32, device=f.device)
+        cnt = torch.empty(shape, dtype=torch.int32, device=f.device) if count else None
+        st = stream if stream is not None else current_stream_handle(f.device)
+        fn = morph_dilate3d if op == 0 else morph_erode3d
+        check(fn(self.handle, vol, sv.c, out.data_ptr(), cnt.data_ptr() if count else None, make_opts(method), st),
+              "morph_dilate3d" if op == 0 else "morph_erode3d")
+        return (out, cnt) if count else out
+
+    def dilate3d(self, f, L, mask, offset, origin, method="auto", count=False, stream=None):
+        """3-D dilation of a [N, D, H, W] (or [D, H, W]) volume by a [kd, kh, kw] SE."""
+        return self._run3d(0, f, L, mask, offset, origin, method, count, stream)
+
+    def erode3d(self, f, L, mask, offset, origin, method="auto", count=False, stream=None):
+        """3-D erosion of a [N, D, H, W] (or [D, H, W]) volume by a [kd, kh, kw] SE."""
+        return self._run3d(1, f, L, mask, offset, origin, method, count, stream)
 
     def composite(self, which, f, L, se, method="auto", stream=None, out=None):
         """which: 'open' | 'close' | 'gradient'."""

@@ -74,3 +74,39 @@ def test_single_point_se_closed_form():
     exp = np.zeros_like(up)
     exp[:, :, 1:, :-1] = up[:, :, :-1, 1:]
     np.testing.assert_allclose(gx.cpu().numpy(), exp, rtol=0, atol=0)
+
+
+def _check_erode(x_np, b_np, mask, origin, L, g_np):
+    from paper_2305_03018_gb300.autograd import erode
+    x = torch.from_numpy(x_np).cuda().requires_grad_(True)
+    b = torch.from_numpy(b_np).cuda().requires_grad_(True)
+    y = erode(x, b, L, mask, origin)
+    y.backward(torch.from_numpy(g_np).cuda())
+    torch.cuda.synchronize()
+    H, W = x_np.shape[-2:]
+    f = x_np.reshape(-1, H, W).astype(np.int32)
+    off = b_np.astype(np.int32)
+    gg = g_np.reshape(-1, H, W).astype(np.float64)
+    E, cE = oracle.erode(f, L, mask, off, origin)
+    gf, gb = oracle.erode_backward(f, L, mask, off, origin, E, cE, gg)
+    sf, sb = oracle.erode_backward(f, L, mask, off, origin, E, cE, np.abs(gg))
+    np.testing.assert_array_equal(y.detach().cpu().numpy().reshape(E.shape).astype(np.int64), E)
+    ntaps = int(np.count_nonzero(mask))
+    gx = x.grad.cpu().numpy().reshape(gf.shape).astype(np.float64)
+    assert (np.abs(gx - gf) <= (ntaps + 2) * U * sf + 1e-30).all(), np.abs(gx - gf).max()
+    gbg = b.grad.cpu().numpy().astype(np.float64)
+    assert (np.abs(gbg - gb) <= 48 * U * np.abs(sb) + U * np.abs(gb) + 1e-30).all(), np.abs(gbg - gb).max()
+    assert (gbg[np.asarray(mask) == 0] == 0).all()
+
+
+def test_c4_layer_erosion_backward():
+    c = wl.c4_layer()
+    _check_erode(c.x, c.b, np.ones((9, 9), np.uint8), c.origin, c.L, c.g)
+
+
+def test_erosion_backward_irregular_se_with_ties():
+    g = wl.rng(33)
+    x = g.integers(0, 4, size=(2, 1, 29, 41)).astype(np.float32)
+    se = wl.se_random(g, 5, 7, 0.6, 2, origin=(3, 1))
+    up = g.standard_normal(x.shape).astype(np.float32)
+    _check_erode(x, se.offset.astype(np.float32), se.mask, se.origin, 4, up)
