@@ -86,7 +86,9 @@ enum morph_method {
     MORPH_AUTO = 0,          /* planner picks the fastest exact back-end */
     MORPH_DIRECT_FP8 = 1,    /* tcgen05 FP8 implicit GEMM, exact by construction */
     MORPH_FFT_F32 = 2,       /* FP32 FFT; refused (E_PRECISION) if the bound fails */
-    MORPH_FFT_F64 = 3        /* FP64 FFT, the plain form of the paper's Step 2 */
+    MORPH_FFT_F64 = 3,       /* FP64 FFT, the plain form of the paper's Step 2 */
+    MORPH_NTT = 4            /* number-theoretic transform mod a prime > |B|: exact integer
+                                convolution (Sec. 2.3), no round-off bound needed */
 };
 
 enum morph_flags {

@@ -297,7 +297,9 @@ __global__ void __launch_bounds__(256) k_fft_cols(const FftArgs a) {
     const cT* out = fft_block<T, cT>(res, other, a.ay, tw, C);
     for (int t = threadIdx.x; t < a.To_y * C; t += blockDim.x) {
         const int c = t % C, q = t / C;
-        if (u0 + c < Nx) plane[static_cast<long long>(q) * Nx + u0 + c] = cconj(out[(q + a.ry) * C + c]);
+        // torus position of output row q is (q + ry) mod Ny (ry < 0 or >= Ny when the origin lies outside the box)
+        const int pos = ((q + a.ry) % Ny + Ny) % Ny;
+        if (u0 + c < Nx) plane[static_cast<long long>(q) * Nx + u0 + c] = cconj(out[pos * C + c]);
     }
 }
 
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(256) k_fft_rows_inv(const FftArgs a) {
     for (int p = threadIdx.x; p < Nx; p += blockDim.x) b0[p] = cconj(row[p]);
     __syncthreads();
     const cT* res = fft_block<T, cT>(b0, b1, a.ax, tw, 1);
-    for (int p = threadIdx.x; p < a.To_x; p += blockDim.x) row[p] = cconj(res[p + a.rx]);
+    for (int p = threadIdx.x; p < a.To_x; p += blockDim.x) row[p] = cconj(res[((p + a.rx) % Nx + Nx) % Nx]);
 }
 
 // Step 3 by direct evaluation, for grey axes short enough that a few

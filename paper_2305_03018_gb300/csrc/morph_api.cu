@@ -205,6 +205,10 @@ static int get_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, in
         p->route = ROUTE_DIRECT;
         int rc = build_direct_plan(ctx, f, se, erode, &p->direct);
         if (rc) return rc;
+    } else if (route == ROUTE_NTT) {
+        p->route = ROUTE_NTT;
+        int rc = build_ntt_plan(ctx, f, se, &p->ntt);
+        if (rc) return rc;
     } else {
         p->route = route;
         int rc = build_fft_plan(ctx, f, se, route == ROUTE_FFT32 ? 4 : 8, unproven, &p->fft);
@@ -230,6 +234,7 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
     if (method == MORPH_DIRECT_FP8) { *route = ROUTE_DIRECT; return MORPH_OK; }
     if (method == MORPH_FFT_F64) { *route = ROUTE_FFT64; return MORPH_OK; }
     if (method == MORPH_FFT_F32) { *route = ROUTE_FFT32; return MORPH_OK; }
+    if (method == MORPH_NTT) { *route = ROUTE_NTT; return MORPH_OK; }
     if (method != MORPH_AUTO) return MORPH_E_INVAL;
     const std::string key = "auto|" + plan_key(f, se, erode, 0);
     auto it = ctx->route_cache.find(key);
@@ -284,6 +289,7 @@ int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, 
     if (rc) return rc;
     const long long npx = static_cast<long long>(f->n) * f->h * f->w;
     if (plan->route == ROUTE_EMPTY) return launch_fill_empty(ctx, out, cnt, npx, erode ? f->L - 1 : 0, st);
+    if (plan->route == ROUTE_NTT) return launch_ntt(ctx, plan->ntt, f, erode, out, cnt, st);
     if (plan->route == ROUTE_FFT32 || plan->route == ROUTE_FFT64)
         return launch_fft(ctx, plan->fft, f, erode, out, cnt, opts ? opts->count_err : nullptr,
                           (opts && (opts->flags & MORPH_F_VALIDATE)) ? 1 : 0, st);
@@ -427,6 +433,17 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         out->tile_h = d.rows_n;
         out->est_flop = d.issued_flop;
         out->workspace_bytes = planes_bytes(f);
+    } else if (route == ROUTE_NTT) {
+        NttPlan q;
+        rc = plan_ntt_tiles(f, &e.se, &q);
+        if (rc) return rc;
+        out->method = MORPH_NTT;
+        out->fft_nx = q.ax.N;
+        out->fft_ny = q.ay.N;
+        out->tile_w = q.To_x;
+        out->tile_h = q.To_y;
+        out->est_flop = q.ops;
+        out->workspace_bytes = q.ws_bytes;
     } else {
         FftPlan q;
         rc = plan_fft_tiles(f, &e.se, route == ROUTE_FFT32 ? 4 : 8, unproven, &q);

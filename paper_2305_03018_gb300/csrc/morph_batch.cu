@@ -89,7 +89,10 @@ int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts*
         off = align_up(off + planes_bytes(&b->items[i].f), 256);
     }
     size_t fft_need = 0;
-    for (int i : b->fft_items) fft_need = std::max(fft_need, b->items[i].plan->fft.ws_bytes);
+    for (int i : b->fft_items) {
+        const Plan& pl = *b->items[i].plan;
+        fft_need = std::max(fft_need, pl.route == ROUTE_NTT ? pl.ntt.ws_bytes : pl.fft.ws_bytes);
+    }
     b->fft_off = off;
     off = align_up(off + fft_need, 256);
     b->total_bytes = std::max<size_t>(off, 256);
@@ -165,8 +168,10 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
         MORPH_CUDA_TRY(cudaMemsetAsync(b->count_err, 0, sizeof(float), st));
     for (int i : b->fft_items) {
         const auto& it = b->items[i];
-        int rc = launch_fft_in(ctx, it.plan->fft, &it.f, it.erode, it.out, it.cnt, b->count_err, b->validate,
-                               ws + b->fft_off, st);
+        int rc = it.plan->route == ROUTE_NTT
+                     ? launch_ntt_in(ctx, it.plan->ntt, &it.f, it.erode, it.out, it.cnt, ws + b->fft_off, st)
+                     : launch_fft_in(ctx, it.plan->fft, &it.f, it.erode, it.out, it.cnt, b->count_err, b->validate,
+                                     ws + b->fft_off, st);
         if (rc) return rc;
     }
     return MORPH_OK;

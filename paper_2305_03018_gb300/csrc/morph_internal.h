@@ -117,13 +117,33 @@ struct FftPlan {
     ~FftPlan();
 };
 
+// ------------------------------------------------ exact NTT route (Step 2)
+struct NttPlan {
+    int taps = 0, R = 0, Rf = 0;  // |B|, degrees, grey-axis length (= grey frequencies)
+    int kh = 0, kw = 0, ry = 0, rx = 0;
+    int To_y = 0, To_x = 0, Rin_y = 0, Win_x = 0;
+    int tiles_y = 0, tiles_x = 0;
+    long long ntiles = 0;
+    int wave_tiles = 0, kgroup = 1, colgroup = 8, pixgroup = 16;
+    size_t buf_bytes = 0, ws_bytes = 0;
+    double ops = 0, bytes = 0;    // estimated integer operations and HBM bytes per call
+    FftAxis ax, ay, ar;
+    uint32_t* tw_x = nullptr;
+    uint32_t* tw_y = nullptr;
+    uint32_t* tw_r = nullptr;
+    uint32_t* wr = nullptr;
+    uint32_t* S = nullptr;
+    ~NttPlan();
+};
+
 // ------------------------------------------------------------------- plans
-enum Route { ROUTE_EMPTY = 0, ROUTE_DIRECT = 1, ROUTE_FFT32 = 2, ROUTE_FFT64 = 3 };
+enum Route { ROUTE_EMPTY = 0, ROUTE_DIRECT = 1, ROUTE_FFT32 = 2, ROUTE_FFT64 = 3, ROUTE_NTT = 4 };
 
 struct Plan {
     int route = ROUTE_EMPTY;
     DirectPlan direct;
     FftPlan fft;
+    NttPlan ntt;
 };
 
 }  // namespace morph
@@ -190,6 +210,13 @@ int launch_fft(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode
                float* count_err, int validate, cudaStream_t st);
 int launch_fft_in(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
                   float* count_err, int validate, void* buf, cudaStream_t st);
+int plan_ntt_tiles(const morph_image* f, const morph_se* se, NttPlan* p);
+double ntt_time_estimate(const NttPlan& p);
+int build_ntt_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, NttPlan* p);
+int launch_ntt(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
+               cudaStream_t st);
+int launch_ntt_in(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
+                  void* buf, cudaStream_t st);
 double fft_error_bound(const FftAxis& ax, const FftAxis& ay, const FftAxis& ar, double sqrtP, int taps, double u);
 
 }  // namespace morph

@@ -22,9 +22,10 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libmorph_gb300.so")
 MORPH_OK, MORPH_E_INVAL, MORPH_E_RANGE, MORPH_E_NOMEM, MORPH_E_PRECISION, MORPH_E_CUDA, MORPH_E_TIMEOUT, \
     MORPH_E_UNSUPPORTED = range(8)
 MORPH_U8, MORPH_U16, MORPH_I32 = 0, 1, 2
-MORPH_AUTO, MORPH_DIRECT_FP8, MORPH_FFT_F32, MORPH_FFT_F64 = 0, 1, 2, 3
+MORPH_AUTO, MORPH_DIRECT_FP8, MORPH_FFT_F32, MORPH_FFT_F64, MORPH_NTT = 0, 1, 2, 3, 4
 MORPH_F_ALLOW_UNPROVEN_F32, MORPH_F_VALIDATE = 1, 2
-METHODS = {"auto": MORPH_AUTO, "direct_fp8": MORPH_DIRECT_FP8, "fft_f32": MORPH_FFT_F32, "fft_f64": MORPH_FFT_F64}
+METHODS = {"auto": MORPH_AUTO, "direct_fp8": MORPH_DIRECT_FP8, "fft_f32": MORPH_FFT_F32, "fft_f64": MORPH_FFT_F64,
+           "ntt": MORPH_NTT}
 
 
 class morph_image(ctypes.Structure):

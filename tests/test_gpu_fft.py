@@ -120,3 +120,14 @@ def test_fp32_tiles_shrink_to_meet_bound(ctx):
 def test_auto_route_is_exact(ctx):
     for p in [wl.c1_small_dilation()]:
         _eq(_run(ctx, p.f, p.L, p.se, "dilate", "auto"), _ref(p.f, p.L, p.se, "dilate"))
+
+
+@pytest.mark.parametrize("method", ["fft_f64", "fft_f32"])
+@pytest.mark.parametrize("origin", [(-3, 9), (8, -5), (-20, -20), (30, 2)])
+def test_origin_outside_the_box(ctx, method, origin):
+    # the output's torus position (q + reach) mod N wraps when the origin lies outside the SE box
+    g = wl.rng(hash(origin) & 0xFFFF)
+    f = g.integers(0, 32, size=(2, 70, 81)).astype(np.uint8)
+    se = wl.se_random(g, 6, 4, 0.6, 4, origin=origin, force_origin=False)
+    for op in ("dilate", "erode"):
+        _eq(_run(ctx, f, 32, se, op, method), _ref(f, 32, se, op))
