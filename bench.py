@@ -372,6 +372,25 @@ def _time_forms(ctx, probs, f_dev, L, ref_outs, px_per_step, stream, steps):
                      "max_count_err": worst, "a_priori_bound_max": max(bounds),
                      "fft_tflops_achieved": fft_flop / (ms * 1e-3) / 1e12,
                      "proven": max(bounds) < 0.5}
+    # the exact number-theoretic transform form (no round-off bound to prove)
+    outs = [torch.empty_like(o) for o in ref_outs]
+
+    def step_ntt():
+        for p, o in zip(probs, outs):
+            (ctx.dilate if p.op == "dilate" else ctx.erode)(f_dev, L, p.se, method="ntt", out=o)
+
+    step_ntt()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step_ntt()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = e0.elapsed_time(e1) / steps
+    res["ntt"] = {"value": px_per_step / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                  "exact": all(bool(torch.equal(o, r)) for o, r in zip(outs, ref_outs))}
     return res
 
 
@@ -449,7 +468,8 @@ def run_config(args, ws, rank, local):
     steps = max(1, args.steps)
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": 1, "higher_is_better": True,
             "data": "synthetic (seeded, paper-shaped)", "workload": args.workload}
-    forms3 = [("direct_fp8", "direct_fp8", {}), ("fft_f32", "fft_f32", {}), ("fft_f64", "fft_f64", {})]
+    forms3 = [("direct_fp8", "direct_fp8", {}), ("fft_f32", "fft_f32", {}), ("fft_f64", "fft_f64", {}),
+              ("ntt", "ntt", {})]
     if args.workload in ("c1", "c3"):
         p = wl.c1_small_dilation() if args.workload == "c1" else wl.c3_full_tonal()
         f = torch.from_numpy(p.f).cuda()
@@ -559,9 +579,10 @@ def run_sweep(args, ws, rank, local):
             se = wl.se_full_random(g, k, L - 1)
             items = [(f, L, se, "dilate", None)]
             forms, skipped = [], {}
-            for name, method in (("auto", "auto"), ("direct_fp8", "direct_fp8"), ("fft_f64", "fft_f64")):
+            for name, method in (("auto", "auto"), ("direct_fp8", "direct_fp8"), ("fft_f64", "fft_f64"),
+                                 ("ntt", "ntt")):
                 est = ctx.plan(f, L, se, method=method)
-                rate = {1: 3.0e15, 2: 2.5e13, 3: 0.9e12}[est.method]
+                rate = {1: 3.0e15, 2: 2.5e13, 3: 0.9e12, 4: 1.6e13}[est.method]
                 if est.est_flop / rate > 20.0:           # keep the sweep within minutes
                     skipped[name] = f"skipped: estimated {est.est_flop / rate:.0f} s per op"
                 else:
@@ -570,7 +591,7 @@ def run_sweep(args, ws, rank, local):
             res.update({k: {"note": v} for k, v in skipped.items()})
             info = ctx.plan(f, L, se, method="auto")
             rows.append({"bits": bits, "image": n, "filter": k,
-                         "auto_method": {1: "direct_fp8", 2: "fft_f32", 3: "fft_f64"}.get(info.method),
+                         "auto_method": {1: "direct_fp8", 2: "fft_f32", 3: "fft_f64", 4: "ntt"}.get(info.method),
                          "s_per_op": {m: (r["ms_per_step"] * 1e-3 if r.get("ms_per_step") else None)
                                       for m, r in res.items()},
                          "exact_vs_first": all(r.get("exact_vs_first", False) for r in res.values()

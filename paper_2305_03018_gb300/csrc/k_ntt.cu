@@ -4,13 +4,14 @@
 // Eq. Obs7 has integer coefficients in [0, |B|], so its convolution computed
 // modulo a prime P > |B| is the exact count, with no round-off bound.
 //
-// P = 2^14 3^6 5^3 + 1 = 1492992001 (prime, < 2^31), so P - 1 is divisible by
-// every transform length 2^a 3^b 5^c <= 2048 with c <= 3, and sums of two
-// residues fit in 32 bits.  omega_N = g^((P-1)/N) with the primitive root
-// g = 11 plays the part of exp(-2 pi i / N).  Products use the Montgomery
-// form (REDC with 2^32): constants (twiddles, the SE spectrum) are stored
-// pre-multiplied by 2^32 mod P, so one REDC of a plain residue by a stored
-// constant gives the plain product.
+// P = 2^13 3^6 5^3 + 1 = 746496001 (prime, < 2^30), so P - 1 is divisible by
+// every transform length 2^a 3^b 5^c <= 2048 with c <= 3.  omega_N =
+// g^((P-1)/N) with the primitive root g = 7 plays the part of exp(-2 pi i / N).
+// Residues are kept lazily in [0, 2P) (sums of two stay below 4P < 2^32) and
+// reduced once where a count is read.  Products by constants (twiddles, radix
+// roots) use Shoup's precomputed quotient; products by the SE spectrum use the
+// Montgomery form (REDC with 2^32), the spectrum being stored multiplied by
+// 2^32 mod P.
 //
 // The data flow follows the FFT route: the grey axis of the umbra (Eq. 7) is
 // one-hot, so its transform is the table omega_Rf^(k f(x)); for each grey
@@ -39,9 +40,11 @@
 
 namespace morph {
 
-constexpr uint32_t kP = 1492992001u;       // 2^14 3^6 5^3 + 1
-constexpr uint32_t kPinv = 3372040191u;    // -P^-1 mod 2^32
-constexpr uint64_t kG = 11u;               // primitive root mod P
+constexpr uint32_t kP = 746496001u;        // 2^13 3^6 5^3 + 1
+constexpr uint32_t kPinv = 1216258047u;    // -P^-1 mod 2^32
+constexpr uint64_t kG = 7u;                // primitive root mod P
+constexpr uint32_t k2P = 2u * kP;
+static_assert(kP < (1u << 30), "lazy residues in [0, 2P) need 4P < 2^32");
 constexpr int kNttMaxN = 2048;
 
 static_assert(static_cast<uint32_t>(kP * kPinv) == 0xFFFFFFFFu, "kPinv must be -P^-1 mod 2^32");
@@ -59,116 +62,139 @@ constexpr uint64_t npow(uint64_t b, uint64_t e) {
 constexpr uint32_t to_mont(uint64_t x) { return static_cast<uint32_t>(((x % kP) << 32) % kP); }
 constexpr uint64_t kInv2 = (kP + 1) / 2;
 
-// radix roots (omega_r = g^((P-1)/r)) and the radix-5 combinations, Montgomery form
+// radix roots omega_r = g^((P-1)/r)
 constexpr uint64_t kW3 = npow(kG, (kP - 1) / 3);
 constexpr uint64_t kW4 = npow(kG, (kP - 1) / 4);
 constexpr uint64_t kW5 = npow(kG, (kP - 1) / 5);
-constexpr uint32_t kW3m = to_mont(kW3);
-constexpr uint32_t kW4m = to_mont(kW4);
-constexpr uint32_t kC1m = to_mont((kW5 + npow(kW5, 4)) % kP * kInv2 % kP);
-constexpr uint32_t kC2m = to_mont((npow(kW5, 2) + npow(kW5, 3)) % kP * kInv2 % kP);
-constexpr uint32_t kS1m = to_mont((kW5 + kP - npow(kW5, 4)) % kP * kInv2 % kP);
-constexpr uint32_t kS2m = to_mont((npow(kW5, 2) + kP - npow(kW5, 3)) % kP * kInv2 % kP);
 
-__device__ __forceinline__ uint32_t madd(uint32_t a, uint32_t b) {
-    const uint32_t s = a + b;
-    return s >= kP ? s - kP : s;
-}
-__device__ __forceinline__ uint32_t msub(uint32_t a, uint32_t b) {
-    const uint32_t s = a + (kP - b);
-    return s >= kP ? s - kP : s;
-}
-// a * bm * 2^-32 mod P for a, bm < P: with bm = b 2^32 mod P this is a b mod P.
-// t = a bm, m = t mod 2^32 * (-P^-1); (t + m P) / 2^32 < 2P; the low words of
-// t and m P sum to 0 or 2^32, a carry exactly when t mod 2^32 != 0.
+// [0, 4P) -> [0, 2P)
+__device__ __forceinline__ uint32_t lz(uint32_t x) { return min(x, x - k2P); }
+__device__ __forceinline__ uint32_t ladd(uint32_t a, uint32_t b) { return lz(a + b); }
+__device__ __forceinline__ uint32_t lsub(uint32_t a, uint32_t b) { return lz(a + k2P - b); }
+// [0, 2P) -> [0, P)
+__device__ __forceinline__ uint32_t canon(uint32_t x) { return min(x, x - kP); }
+// a * bm * 2^-32 mod P in [0, 2P) for a, bm < 2P (Montgomery REDC): with
+// bm = b 2^32 mod P this is a b mod P.  t = a bm < 4P^2 < 2^62, m = (t mod
+// 2^32) (-P^-1) mod 2^32; (t + m P) / 2^32 < P (4P / 2^32 + 1) < 2P.  The low
+// words of t and m P sum to 0 or 2^32, a carry exactly when t mod 2^32 != 0.
 __device__ __forceinline__ uint32_t mmul(uint32_t a, uint32_t bm) {
     const uint64_t t = static_cast<uint64_t>(a) * bm;
     const uint32_t lo = static_cast<uint32_t>(t), hi = static_cast<uint32_t>(t >> 32);
     const uint32_t m = lo * kPinv;
-    const uint32_t u = hi + __umulhi(m, kP) + (lo != 0u ? 1u : 0u);
-    return u >= kP ? u - kP : u;
+    return hi + __umulhi(m, kP) + (lo != 0u ? 1u : 0u);
 }
+// x w mod P in [0, 2P) for any 32-bit x and a constant w < P with
+// wq = floor(w 2^32 / P) (Shoup): x w - floor(x wq / 2^32) P lies in [0, 2P).
+__device__ __forceinline__ uint32_t lmul(uint32_t x, uint32_t w, uint32_t wq) {
+    return x * w - __umulhi(x, wq) * kP;
+}
+constexpr uint32_t shoup_q(uint64_t w) { return static_cast<uint32_t>((w << 32) / kP); }
 
-// Radix-r forward DFTs mod P, y_k = sum_j v_j omega_r^(jk), in registers.
+constexpr uint64_t kC1 = (kW5 + npow(kW5, 4)) % kP * kInv2 % kP;
+constexpr uint64_t kC2 = (npow(kW5, 2) + npow(kW5, 3)) % kP * kInv2 % kP;
+constexpr uint64_t kS1 = (kW5 + kP - npow(kW5, 4)) % kP * kInv2 % kP;
+constexpr uint64_t kS2 = (npow(kW5, 2) + kP - npow(kW5, 3)) % kP * kInv2 % kP;
+// (value, Shoup quotient) of the radix constants, as compile-time constants
+struct NttConst {
+    uint32_t w, q;
+};
+constexpr NttConst nconst(uint64_t c) { return NttConst{static_cast<uint32_t>(c), shoup_q(c)}; }
+constexpr NttConst kW3c = nconst(kW3), kW4c = nconst(kW4);
+constexpr NttConst kC1c = nconst(kC1), kC2c = nconst(kC2), kS1c = nconst(kS1), kS2c = nconst(kS2);
+#define NTT_K(x) x##c.w, x##c.q
+
+// Radix-r forward DFTs mod P, y_k = sum_j v_j omega_r^(jk), in registers;
+// inputs and outputs in [0, 2P).
 __device__ __forceinline__ void ndft2(uint32_t* v) {
     const uint32_t a = v[0], b = v[1];
-    v[0] = madd(a, b);
-    v[1] = msub(a, b);
+    v[0] = ladd(a, b);
+    v[1] = lsub(a, b);
 }
 __device__ __forceinline__ void ndft4(uint32_t* v) {
     // omega_4^2 = -1
-    const uint32_t s02 = madd(v[0], v[2]), d02 = msub(v[0], v[2]);
-    const uint32_t s13 = madd(v[1], v[3]), d13 = mmul(msub(v[1], v[3]), kW4m);
-    v[0] = madd(s02, s13);
-    v[2] = msub(s02, s13);
-    v[1] = madd(d02, d13);
-    v[3] = msub(d02, d13);
+    const uint32_t s02 = ladd(v[0], v[2]), d02 = lsub(v[0], v[2]);
+    const uint32_t s13 = ladd(v[1], v[3]), d13 = lmul(v[1] + k2P - v[3], NTT_K(kW4));
+    v[0] = ladd(s02, s13);
+    v[2] = lsub(s02, s13);
+    v[1] = ladd(d02, d13);
+    v[3] = lsub(d02, d13);
 }
 __device__ __forceinline__ void ndft3(uint32_t* v) {
     // omega^2 = -1 - omega: y1 = (v0 - v2) + omega (v1 - v2), y2 = (v0 - v1) - omega (v1 - v2)
-    const uint32_t t = mmul(msub(v[1], v[2]), kW3m);
-    const uint32_t y0 = madd(madd(v[0], v[1]), v[2]);
-    const uint32_t y1 = madd(msub(v[0], v[2]), t);
-    const uint32_t y2 = msub(msub(v[0], v[1]), t);
+    const uint32_t t = lmul(v[1] + k2P - v[2], NTT_K(kW3));
+    const uint32_t y0 = ladd(ladd(v[0], v[1]), v[2]);
+    const uint32_t y1 = ladd(lsub(v[0], v[2]), t);
+    const uint32_t y2 = lsub(lsub(v[0], v[1]), t);
     v[0] = y0;
     v[1] = y1;
     v[2] = y2;
 }
 __device__ __forceinline__ void ndft5(uint32_t* v) {
     // C_j = (w^j + w^-j) / 2, S_j = (w^j - w^-j) / 2 with w = omega_5
-    const uint32_t b1 = madd(v[1], v[4]), b2 = madd(v[2], v[3]);
-    const uint32_t d1 = msub(v[1], v[4]), d2 = msub(v[2], v[3]);
+    const uint32_t b1 = ladd(v[1], v[4]), b2 = ladd(v[2], v[3]);
+    const uint32_t d1 = v[1] + k2P - v[4], d2 = v[2] + k2P - v[3];     // < 4P: Shoup inputs
     const uint32_t a0 = v[0];
-    const uint32_t A1 = madd(a0, madd(mmul(b1, kC1m), mmul(b2, kC2m)));
-    const uint32_t B1 = madd(mmul(d1, kS1m), mmul(d2, kS2m));
-    const uint32_t A2 = madd(a0, madd(mmul(b1, kC2m), mmul(b2, kC1m)));
-    const uint32_t B2 = msub(mmul(d1, kS2m), mmul(d2, kS1m));
-    v[0] = madd(a0, madd(b1, b2));
-    v[1] = madd(A1, B1);
-    v[4] = msub(A1, B1);
-    v[2] = madd(A2, B2);
-    v[3] = msub(A2, B2);
+    const uint32_t A1 = ladd(a0, ladd(lmul(b1, NTT_K(kC1)), lmul(b2, NTT_K(kC2))));
+    const uint32_t B1 = ladd(lmul(d1, NTT_K(kS1)), lmul(d2, NTT_K(kS2)));
+    const uint32_t A2 = ladd(a0, ladd(lmul(b1, NTT_K(kC2)), lmul(b2, NTT_K(kC1))));
+    const uint32_t B2 = lsub(lmul(d1, NTT_K(kS2)), lmul(d2, NTT_K(kS1)));
+    v[0] = ladd(a0, ladd(b1, b2));
+    v[1] = ladd(A1, B1);
+    v[4] = lsub(A1, B1);
+    v[2] = ladd(A2, B2);
+    v[3] = lsub(A2, B2);
 }
 
-// One Stockham stage of radix R over `batch` interleaved transforms of length
-// N (element p of transform c at p * batch + c).  tw[m] = omega_N^m, Montgomery.
-template <int R>
+constexpr int ilog2c(int b) { return b <= 1 ? 0 : 1 + ilog2c(b / 2); }
+// element p of transform c of a batch of B lives at p * pitch(B) + c; the odd
+// pitch keeps column reads (fixed c, consecutive p) free of bank conflicts
+constexpr int npitch(int B) { return B == 1 ? 1 : B + 1; }
+
+// One Stockham stage of radix R over B interleaved transforms of length N.
+// tw[m] = (omega_N^m, Shoup quotient).
+template <int R, int B>
 __device__ __forceinline__ void ntt_stage(const uint32_t* __restrict__ x, uint32_t* __restrict__ y, int N, int Ns,
-                                          const uint32_t* __restrict__ tw, int batch) {
+                                          uint32_t nsm, int tstep, const uint2* __restrict__ tw) {
+    constexpr int PB = npitch(B);
+    constexpr int LB = ilog2c(B);
     const int M = N / R;
-    const int total = M * batch;
-    const int tstep = N / (Ns * R);
+    const int total = M * B;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int c = t % batch;
-        const int j = t / batch;
-        const int k = j % Ns;
+        const int c = t & (B - 1);
+        const int j = t >> LB;
+        const int g = Ns == 1 ? j : static_cast<int>(__umulhi(static_cast<uint32_t>(j), nsm));   // j / Ns
+        const int k = j - g * Ns;
         uint32_t v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = x[(j + r * M) * batch + c];
+        for (int r = 0; r < R; ++r) v[r] = x[(j + r * M) * PB + c];
         if (Ns > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = mmul(v[r], tw[r * k * tstep]);
+            for (int r = 1; r < R; ++r) {
+                const uint2 w = tw[r * k * tstep];
+                v[r] = lmul(v[r], w.x, w.y);
+            }
         }
         if (R == 2) ndft2(v);
         if (R == 3) ndft3(v);
         if (R == 4) ndft4(v);
         if (R == 5) ndft5(v);
-        const int d = (j / Ns) * Ns * R + k;
+        const int d = g * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) y[(d + r * Ns) * batch + c] = v[r];
+        for (int r = 0; r < R; ++r) y[(d + r * Ns) * PB + c] = v[r];
     }
 }
 
-// Forward NTT of `batch` interleaved transforms in a (scratch b); returns the
-// buffer holding the result.  Block-wide; ends with a barrier.
-__device__ uint32_t* ntt_block(uint32_t* a, uint32_t* b, const FftAxis& ax, const uint32_t* tw, int batch) {
+// Forward NTT of B interleaved transforms in a (scratch b); returns the buffer
+// holding the result.  Block-wide; ends with a barrier.
+template <int B>
+__device__ uint32_t* ntt_block(uint32_t* a, uint32_t* b, const NttAxis& ax, const uint2* tw) {
     int Ns = 1;
     for (int s = 0; s < ax.nst; ++s) {
         const int R = ax.rad[s];
-        if (R == 4) ntt_stage<4>(a, b, ax.N, Ns, tw, batch);
-        else if (R == 2) ntt_stage<2>(a, b, ax.N, Ns, tw, batch);
-        else if (R == 3) ntt_stage<3>(a, b, ax.N, Ns, tw, batch);
-        else ntt_stage<5>(a, b, ax.N, Ns, tw, batch);
+        if (R == 4) ntt_stage<4, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
+        else if (R == 2) ntt_stage<2, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
+        else if (R == 3) ntt_stage<3, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
+        else ntt_stage<5, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
         __syncthreads();
         Ns *= R;
         uint32_t* t = a;
@@ -186,24 +212,22 @@ struct NttArgs {
     int L, flip, erode;
     // method
     int R, Rf;                      // degrees, grey-axis length (= grey frequencies)
-    FftAxis ar, ax, ay;
+    uint32_t rfm;                   // ceil(2^32 / Rf)
+    NttAxis ar, ax, ay;
     int To_y, To_x, Rin_y, Win_x;   // output tile, input tile (To + k - 1)
     int ry, rx;                     // SE reach below / right: kh - 1 - oy, kw - 1 - ox
     int tiles_x, tiles_y;
     long long tile0;                // first global tile of this wave
     int wave_tiles;
-    const uint32_t* tw_x;           // omega_Nx^m, Montgomery
-    const uint32_t* tw_y;           // omega_Ny^m, Montgomery
-    const uint32_t* tw_r;           // omega_Rf^m, Montgomery
-    const uint32_t* wr;             // omega_Rf^m, plain (encoder table)
-    const uint32_t* S;              // SE spectrum / (Rf Ny Nx), Montgomery, [Rf][Ny][Nx]
+    const uint2* tw_x;              // (omega_Nx^m, Shoup quotient)
+    const uint2* tw_y;
+    const uint2* tw_r;
+    const uint32_t* wr;             // omega_Rf^m (encoder table)
+    const uint32_t* S;              // SE spectrum / (Rf Ny Nx), Montgomery form, [Rf][Ny][Nx]
     uint32_t* buf;                  // [wave_tiles][Rf][Ny][Nx]
     int32_t* out;
     int32_t* out_cnt;
     unsigned int* err;
-    int kgroup;                     // grey frequencies per pass in the row kernels
-    int colgroup;                   // columns per CTA in k_ntt_cols
-    int pixgroup;                   // pixels per CTA in k_ntt_range
 };
 
 __device__ __forceinline__ int ntt_load_px(const void* src, int dtype, long long idx) {
@@ -220,18 +244,26 @@ __device__ __forceinline__ void ntt_tile_origin(const NttArgs& a, long long gt, 
     *x0 = (rem % a.tiles_x) * a.To_x;
 }
 
-// grid (Rin_y, wave_tiles): input row rho of tile tl, every grey frequency
+__device__ __forceinline__ void ntt_copy_tw(uint2* dst, const uint2* src, int n) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = src[j];
+}
+
+// grid (Rin_y, wave_tiles): input row rho of tile tl, every grey frequency, B at a time
+template <int B>
 __global__ void __launch_bounds__(256) k_ntt_rows_fwd(const NttArgs a) {
+    constexpr int PB = npitch(B);
     extern __shared__ __align__(16) unsigned char sm[];
-    const int Nx = a.ax.N, KB = a.kgroup;
-    uint32_t* tw = reinterpret_cast<uint32_t*>(sm);
-    uint32_t* b0 = tw + Nx;
-    uint32_t* b1 = b0 + KB * Nx;
-    int* lev = reinterpret_cast<int*>(b1 + KB * Nx);
+    const int Nx = a.ax.N, Rf = a.Rf;
+    uint2* tw = reinterpret_cast<uint2*>(sm);
+    uint32_t* wr = reinterpret_cast<uint32_t*>(tw + Nx);
+    int* lev = reinterpret_cast<int*>(wr + Rf);
+    uint32_t* b0 = reinterpret_cast<uint32_t*>(lev + Nx);
+    uint32_t* b1 = b0 + Nx * PB;
     const int rho = blockIdx.x, tl = blockIdx.y;
     int n, y0, x0;
     ntt_tile_origin(a, a.tile0 + tl, &n, &y0, &x0);
-    for (int j = threadIdx.x; j < Nx; j += blockDim.x) tw[j] = a.tw_x[j];
+    ntt_copy_tw(tw, a.tw_x, Nx);
+    for (int j = threadIdx.x; j < Rf; j += blockDim.x) wr[j] = a.wr[j];
     const int iy = y0 - a.ry + rho;
     bool bad = false;
     for (int p = threadIdx.x; p < Nx; p += blockDim.x) {
@@ -247,103 +279,148 @@ __global__ void __launch_bounds__(256) k_ntt_rows_fwd(const NttArgs a) {
     if (bad) atomicOr(a.err, MORPH_DEVERR_RANGE);
     __syncthreads();
     const long long plane = static_cast<long long>(a.ay.N) * Nx;
-    uint32_t* dst = a.buf + static_cast<long long>(tl) * a.Rf * plane + static_cast<long long>(rho) * Nx;
-    for (int k0 = 0; k0 < a.Rf; k0 += KB) {
-        const int kb = min(KB, a.Rf - k0);
-        for (int t = threadIdx.x; t < kb * Nx; t += blockDim.x) {
-            const int c = t % kb, p = t / kb;
+    uint32_t* dst = a.buf + static_cast<long long>(tl) * Rf * plane + static_cast<long long>(rho) * Nx;
+    for (int k0 = 0; k0 < Rf; k0 += B) {
+        for (int t = threadIdx.x; t < B * Nx; t += blockDim.x) {
+            const int c = t & (B - 1), p = t >> ilog2c(B);
             const int l = lev[p];
-            b0[t] = l >= 0 ? a.wr[((k0 + c) * l) % a.Rf] : 0u;
+            const uint32_t e = static_cast<uint32_t>(k0 + c) * static_cast<uint32_t>(l < 0 ? 0 : l);
+            const uint32_t m = e - __umulhi(e, a.rfm) * static_cast<uint32_t>(Rf);       // e mod Rf
+            b0[p * PB + c] = (l >= 0 && k0 + c < Rf) ? wr[m] : 0u;
         }
         __syncthreads();
-        const uint32_t* res = ntt_block(b0, b1, a.ax, tw, kb);
-        for (int t = threadIdx.x; t < kb * Nx; t += blockDim.x) {
-            const int c = t / Nx, p = t % Nx;
-            dst[(k0 + c) * plane + p] = res[p * kb + c];
-        }
+        const uint32_t* res = ntt_block<B>(b0, b1, a.ax, tw);
+        const int kb = min(B, Rf - k0);
+        for (int c = 0; c < kb; ++c)
+            for (int p = threadIdx.x; p < Nx; p += blockDim.x) dst[(k0 + c) * plane + p] = res[p * PB + c];
         __syncthreads();
     }
 }
 
-// grid (ceil(Nx / C), Rf, wave_tiles)
-__global__ void __launch_bounds__(256) k_ntt_cols(const NttArgs a) {
+// grid (wave_tiles, ceil(Nx / C), Rf): the tiles of one (column group, k) run
+// together, so they read that strip of the SE spectrum from L2
+template <int C>
+__global__ void __launch_bounds__(512) k_ntt_cols(const NttArgs a) {
+    constexpr int PC = npitch(C);
     extern __shared__ __align__(16) unsigned char sm[];
-    const int Ny = a.ay.N, Nx = a.ax.N, C = a.colgroup;
-    uint32_t* tw = reinterpret_cast<uint32_t*>(sm);
-    uint32_t* b0 = tw + Ny;
-    uint32_t* b1 = b0 + Ny * C;
-    const int u0 = blockIdx.x * C, k = blockIdx.y, tl = blockIdx.z;
-    for (int j = threadIdx.x; j < Ny; j += blockDim.x) tw[j] = a.tw_y[j];
+    const int Ny = a.ay.N, Nx = a.ax.N;
+    uint2* tw = reinterpret_cast<uint2*>(sm);
+    uint32_t* b0 = reinterpret_cast<uint32_t*>(tw + Ny);
+    uint32_t* b1 = b0 + Ny * PC;
+    const int tl = blockIdx.x, u0 = blockIdx.y * C, k = blockIdx.z;
+    ntt_copy_tw(tw, a.tw_y, Ny);
     uint32_t* plane = a.buf + (static_cast<long long>(tl) * a.Rf + k) * Ny * Nx;
-    for (int t = threadIdx.x; t < Ny * C; t += blockDim.x) {
-        const int c = t % C, rho = t / C;
-        b0[t] = (rho < a.Rin_y && u0 + c < Nx) ? plane[static_cast<long long>(rho) * Nx + u0 + c] : 0u;
+    // four independent loads in flight per thread
+    for (int t0 = threadIdx.x; t0 < Ny * C; t0 += 4 * blockDim.x) {
+        uint32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * blockDim.x;
+            const int c = t & (C - 1), rho = t >> ilog2c(C);
+            v[u] = (rho < a.Rin_y && u0 + c < Nx) ? plane[static_cast<long long>(rho) * Nx + u0 + c] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t < Ny * C) b0[(t >> ilog2c(C)) * PC + (t & (C - 1))] = v[u];
+        }
     }
     __syncthreads();
-    uint32_t* res = ntt_block(b0, b1, a.ay, tw, C);
-    uint32_t* other = (res == b0) ? b1 : b0;
     const uint32_t* S = a.S + static_cast<long long>(k) * Ny * Nx;
+    // pull this CTA's strip of the SE spectrum towards L2 while the column transforms run
+    for (int v = threadIdx.x; v < Ny; v += blockDim.x)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(S + static_cast<long long>(v) * Nx + u0));
+    uint32_t* res = ntt_block<C>(b0, b1, a.ay, tw);
+    uint32_t* other = (res == b0) ? b1 : b0;
     for (int t = threadIdx.x; t < Ny * C; t += blockDim.x) {
-        const int c = t % C, v = t / C;
-        if (u0 + c < Nx) res[t] = mmul(res[t], S[static_cast<long long>(v) * Nx + u0 + c]);
+        const int c = t & (C - 1), v = t >> ilog2c(C);
+        if (u0 + c < Nx) res[v * PC + c] = mmul(res[v * PC + c], S[static_cast<long long>(v) * Nx + u0 + c]);
     }
     __syncthreads();
-    const uint32_t* o = ntt_block(res, other, a.ay, tw, C);
+    const uint32_t* o = ntt_block<C>(res, other, a.ay, tw);
+    // torus position of output row q is (q + ry) mod Ny (ry < 0 or >= Ny when the origin lies outside the box)
+    const int base = ((a.ry % Ny) + Ny) % Ny;
     for (int t = threadIdx.x; t < a.To_y * C; t += blockDim.x) {
-        const int c = t % C, q = t / C;
-        // torus position of output row q is (q + ry) mod Ny (ry < 0 or >= Ny when the origin lies outside the box)
-        const int pos = ((q + a.ry) % Ny + Ny) % Ny;
+        const int c = t & (C - 1), q = t >> ilog2c(C);
+        int pos = base + q;
+        while (pos >= Ny) pos -= Ny;
         const int idx = pos == 0 ? 0 : Ny - pos;
-        if (u0 + c < Nx) plane[static_cast<long long>(q) * Nx + u0 + c] = o[idx * C + c];
+        if (u0 + c < Nx) plane[static_cast<long long>(q) * Nx + u0 + c] = o[idx * PC + c];
     }
 }
 
-// grid (To_y, ceil(Rf / KB), wave_tiles): output row q, a group of grey frequencies
+// grid (To_y, ceil(Rf / B), wave_tiles): output row q, B grey frequencies
+template <int B>
 __global__ void __launch_bounds__(256) k_ntt_rows_inv(const NttArgs a) {
+    constexpr int PB = npitch(B);
     extern __shared__ __align__(16) unsigned char sm[];
-    const int Nx = a.ax.N, KB = a.kgroup;
-    uint32_t* tw = reinterpret_cast<uint32_t*>(sm);
-    uint32_t* b0 = tw + Nx;
-    uint32_t* b1 = b0 + KB * Nx;
-    const int q = blockIdx.x, k0 = blockIdx.y * KB, tl = blockIdx.z;
-    const int kb = min(KB, a.Rf - k0);
-    for (int j = threadIdx.x; j < Nx; j += blockDim.x) tw[j] = a.tw_x[j];
+    const int Nx = a.ax.N;
+    uint2* tw = reinterpret_cast<uint2*>(sm);
+    uint32_t* b0 = reinterpret_cast<uint32_t*>(tw + Nx);
+    uint32_t* b1 = b0 + Nx * PB;
+    const int q = blockIdx.x, k0 = blockIdx.y * B, tl = blockIdx.z;
+    const int kb = min(B, a.Rf - k0);
+    ntt_copy_tw(tw, a.tw_x, Nx);
     const long long plane = static_cast<long long>(a.ay.N) * Nx;
     uint32_t* rows = a.buf + (static_cast<long long>(tl) * a.Rf + k0) * plane + static_cast<long long>(q) * Nx;
-    for (int t = threadIdx.x; t < kb * Nx; t += blockDim.x) {
-        const int c = t / Nx, p = t % Nx;
-        b0[p * kb + c] = rows[c * plane + p];
-    }
+    for (int c = 0; c < B; ++c)
+        for (int p0 = threadIdx.x; p0 < Nx; p0 += 4 * blockDim.x) {
+            uint32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + u * blockDim.x;
+                v[u] = (c < kb && p < Nx) ? rows[c * plane + p] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + u * blockDim.x;
+                if (p < Nx) b0[p * PB + c] = v[u];
+            }
+        }
     __syncthreads();
-    const uint32_t* res = ntt_block(b0, b1, a.ax, tw, kb);
-    for (int t = threadIdx.x; t < kb * a.To_x; t += blockDim.x) {
-        const int c = t / a.To_x, p = t % a.To_x;
-        const int pos = ((p + a.rx) % Nx + Nx) % Nx;
-        const int idx = pos == 0 ? 0 : Nx - pos;
-        rows[c * plane + p] = res[idx * kb + c];
-    }
+    const uint32_t* res = ntt_block<B>(b0, b1, a.ax, tw);
+    const int base = ((a.rx % Nx) + Nx) % Nx;
+    for (int c = 0; c < kb; ++c)
+        for (int p = threadIdx.x; p < a.To_x; p += blockDim.x) {
+            int pos = base + p;
+            while (pos >= Nx) pos -= Nx;
+            const int idx = pos == 0 ? 0 : Nx - pos;
+            rows[c * plane + p] = res[idx * PB + c];
+        }
 }
 
 // grid (ceil(To_x / C), To_y, wave_tiles): grey-axis inverse NTT of C pixels
 // of output row q, then the top degree with a nonzero count (Eq. 9).
-__global__ void __launch_bounds__(256) k_ntt_range(const NttArgs a) {
+template <int C>
+__global__ void __launch_bounds__(512) k_ntt_range(const NttArgs a) {
+    constexpr int PC = npitch(C);
     extern __shared__ __align__(16) unsigned char sm[];
-    const int Rf = a.Rf, C = a.pixgroup, Nx = a.ax.N, Ny = a.ay.N;
-    uint32_t* tw = reinterpret_cast<uint32_t*>(sm);
-    uint32_t* b0 = tw + Rf;
-    uint32_t* b1 = b0 + Rf * C;
+    const int Rf = a.Rf, Nx = a.ax.N, Ny = a.ay.N;
+    uint2* tw = reinterpret_cast<uint2*>(sm);
+    uint32_t* b0 = reinterpret_cast<uint32_t*>(tw + Rf);
+    uint32_t* b1 = b0 + Rf * PC;
     const int x0 = blockIdx.x * C, q = blockIdx.y, tl = blockIdx.z;
     int n, y0, tx0;
     ntt_tile_origin(a, a.tile0 + tl, &n, &y0, &tx0);
-    for (int j = threadIdx.x; j < Rf; j += blockDim.x) tw[j] = a.tw_r[j];
+    ntt_copy_tw(tw, a.tw_r, Rf);
     const long long kstride = static_cast<long long>(Ny) * Nx;
     const uint32_t* base = a.buf + static_cast<long long>(tl) * Rf * kstride + static_cast<long long>(q) * Nx;
-    for (int t = threadIdx.x; t < Rf * C; t += blockDim.x) {
-        const int c = t % C, k = t / C;
-        b0[t] = (x0 + c < a.To_x) ? base[k * kstride + x0 + c] : 0u;
+    for (int t0 = threadIdx.x; t0 < Rf * C; t0 += 4 * blockDim.x) {
+        uint32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * blockDim.x;
+            const int c = t & (C - 1), k = t >> ilog2c(C);
+            v[u] = (t < Rf * C && x0 + c < a.To_x) ? base[k * kstride + x0 + c] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t < Rf * C) b0[(t >> ilog2c(C)) * PC + (t & (C - 1))] = v[u];
+        }
     }
     __syncthreads();
-    const uint32_t* res = ntt_block(b0, b1, a.ar, tw, C);
+    const uint32_t* res = ntt_block<C>(b0, b1, a.ar, tw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int c = warp; c < C; c += nwarps) {
         const int xo = x0 + c;
@@ -354,11 +431,7 @@ __global__ void __launch_bounds__(256) k_ntt_range(const NttArgs a) {
         for (int d0 = ((a.R - 1) / 32) * 32; d0 >= 0 && D < 0; d0 -= 32) {
             const int d = d0 + lane;
             uint32_t v = 0;
-            if (d < a.R) {
-                int idx = Rf - d;
-                if (idx >= Rf) idx -= Rf;
-                v = res[idx * C + c];
-            }
+            if (d < a.R) v = canon(res[(d == 0 ? 0 : Rf - d) * PC + c]);
             const unsigned m = __ballot_sync(0xffffffffu, v != 0u);
             if (m) {
                 const int top = 31 - __clz(m);
@@ -394,43 +467,47 @@ __global__ void k_ntt_se_scatter(uint32_t* planes, int Rf, int Ny, int Nx, const
 }
 
 // In-place forward NTT of every row of Rf planes (grid (Ny, Rf)).
-__global__ void __launch_bounds__(256) k_ntt_plane_rows(uint32_t* planes, FftAxis ax, const uint32_t* gtw, int Ny) {
+__global__ void __launch_bounds__(256) k_ntt_plane_rows(uint32_t* planes, NttAxis ax, const uint2* gtw, int Ny) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Nx = ax.N;
-    uint32_t* tw = reinterpret_cast<uint32_t*>(sm);
-    uint32_t* b0 = tw + Nx;
+    uint2* tw = reinterpret_cast<uint2*>(sm);
+    uint32_t* b0 = reinterpret_cast<uint32_t*>(tw + Nx);
     uint32_t* b1 = b0 + Nx;
-    for (int j = threadIdx.x; j < Nx; j += blockDim.x) tw[j] = gtw[j];
+    ntt_copy_tw(tw, gtw, Nx);
     uint32_t* p = planes + (static_cast<long long>(blockIdx.y) * Ny + blockIdx.x) * Nx;
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) b0[j] = p[j];
     __syncthreads();
-    const uint32_t* res = ntt_block(b0, b1, ax, tw, 1);
+    const uint32_t* res = ntt_block<1>(b0, b1, ax, tw);
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) p[j] = res[j];
 }
 
-// In-place forward NTT of every column of Rf planes (grid (ceil(Nx / C), Rf)).
-__global__ void __launch_bounds__(256) k_ntt_plane_cols(uint32_t* planes, FftAxis ay, const uint32_t* gtw, int Nx,
-                                                        int C) {
+// In-place forward NTT of every column of Rf planes (grid (ceil(Nx / 8), Rf)).
+__global__ void __launch_bounds__(256) k_ntt_plane_cols(uint32_t* planes, NttAxis ay, const uint2* gtw, int Nx) {
+    constexpr int C = 8, PC = npitch(C);
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = ay.N;
-    uint32_t* tw = reinterpret_cast<uint32_t*>(sm);
-    uint32_t* b0 = tw + Ny;
-    uint32_t* b1 = b0 + Ny * C;
+    uint2* tw = reinterpret_cast<uint2*>(sm);
+    uint32_t* b0 = reinterpret_cast<uint32_t*>(tw + Ny);
+    uint32_t* b1 = b0 + Ny * PC;
     const int u0 = blockIdx.x * C;
-    for (int j = threadIdx.x; j < Ny; j += blockDim.x) tw[j] = gtw[j];
+    ntt_copy_tw(tw, gtw, Ny);
     uint32_t* p = planes + static_cast<long long>(blockIdx.y) * Ny * Nx;
-    for (int t = threadIdx.x; t < Ny * C; t += blockDim.x)
-        b0[t] = (u0 + t % C < Nx) ? p[static_cast<long long>(t / C) * Nx + u0 + t % C] : 0u;
+    for (int t = threadIdx.x; t < Ny * C; t += blockDim.x) {
+        const int c = t & (C - 1), r = t >> ilog2c(C);
+        b0[r * PC + c] = (u0 + c < Nx) ? p[static_cast<long long>(r) * Nx + u0 + c] : 0u;
+    }
     __syncthreads();
-    const uint32_t* res = ntt_block(b0, b1, ay, tw, C);
-    for (int t = threadIdx.x; t < Ny * C; t += blockDim.x)
-        if (u0 + t % C < Nx) p[static_cast<long long>(t / C) * Nx + u0 + t % C] = res[t];
+    const uint32_t* res = ntt_block<C>(b0, b1, ay, tw);
+    for (int t = threadIdx.x; t < Ny * C; t += blockDim.x) {
+        const int c = t & (C - 1), r = t >> ilog2c(C);
+        if (u0 + c < Nx) p[static_cast<long long>(r) * Nx + u0 + c] = res[r * PC + c];
+    }
 }
 
 // S <- S * q * 2^-32: with q = (Rf Ny Nx)^-1 2^64 mod P, the Montgomery form of S / (Rf Ny Nx)
 __global__ void k_ntt_to_mont(uint32_t* s, long long n, uint32_t q) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        s[i] = mmul(s[i], q);
+        s[i] = canon(mmul(s[i], q));
 }
 
 }  // namespace morph
@@ -445,8 +522,9 @@ NttPlan::~NttPlan() {
 
 static uint64_t hpow(uint64_t b, uint64_t e) { return npow(b, e); }
 
-// N = 2^a 3^b 5^c with c <= 3 (P - 1 = 2^14 3^6 5^3), stages 4, 2, 3, 5
-static bool ntt_factor(int N, FftAxis* ax) {
+// N = 2^a 3^b 5^c with c <= 3 (P - 1 = 2^14 3^6 5^3), stages 4, 2, 3, 5, with
+// each stage's twiddle stride and the division magic for Ns
+static bool ntt_factor(int N, NttAxis* ax) {
     if (N < 1 || N > kNttMaxN) return false;
     ax->N = N;
     ax->nst = 0;
@@ -455,36 +533,78 @@ static bool ntt_factor(int N, FftAxis* ax) {
     while (m % 2 == 0) { m /= 2; ++f2; }
     while (m % 3 == 0) { m /= 3; ++f3; }
     while (m % 5 == 0) { m /= 5; ++f5; }
-    if (m != 1 || f5 > 3 || f3 > 6) return false;
+    if (m != 1 || f5 > 3 || f3 > 6 || f4 + f2 + f3 + f5 > 16) return false;
     for (int i = 0; i < f4; ++i) ax->rad[ax->nst++] = 4;
     for (int i = 0; i < f2; ++i) ax->rad[ax->nst++] = 2;
     for (int i = 0; i < f3; ++i) ax->rad[ax->nst++] = 3;
     for (int i = 0; i < f5; ++i) ax->rad[ax->nst++] = 5;
-    return ax->nst <= 16;
+    int Ns = 1;
+    for (int s = 0; s < ax->nst; ++s) {
+        ax->tstep[s] = N / (Ns * ax->rad[s]);
+        // ceil(2^32 / Ns): floor(j * nsm / 2^32) = j / Ns exactly while j * Ns < 2^32
+        ax->nsm[s] = Ns == 1 ? 0u : static_cast<uint32_t>(((uint64_t(1) << 32) + Ns - 1) / Ns);
+        Ns *= ax->rad[s];
+    }
+    return true;
 }
 
+// smallest supported transform length >= n (0 if above 2048)
 static int ntt_size_at_least(int n) {
-    FftAxis t;
-    for (int m = std::max(n, 1); m <= kNttMaxN; ++m)
-        if (ntt_factor(m, &t)) return m;
-    return 0;
+    static std::vector<int> next;
+    if (next.empty()) {
+        next.assign(kNttMaxN + 2, 0);
+        NttAxis t;
+        for (int m = kNttMaxN; m >= 1; --m) next[m] = ntt_factor(m, &t) ? m : next[m + 1];
+    }
+    n = std::max(n, 1);
+    return n > kNttMaxN ? 0 : next[n];
 }
 
-// integer operations per element of one transform (Montgomery product ~6, add/sub ~2)
-static double ntt_ops(const FftAxis& a) {
+// integer instructions per element of one transform: per stage, the twiddle
+// products (Shoup, ~5), the radix's own products and the modular sums (~3)
+static double ntt_ops(const NttAxis& a) {
     double per = 0;
     for (int s = 0; s < a.nst; ++s) {
         const int r = a.rad[s];
-        per += r == 2 ? 5.0 : r == 4 ? 8.0 : r == 3 ? 9.0 : 20.0;
+        per += r == 2 ? 6.0 : r == 4 ? 11.0 : r == 3 ? 12.0 : 24.0;
     }
     return per * a.N;
 }
 
-static size_t ntt_smem_rows(int N, int kg) { return 4 * (static_cast<size_t>(N) * (1 + 2 * kg) + N); }
-static size_t ntt_smem_cols(int N, int C) { return 4 * static_cast<size_t>(N) * (1 + 2 * C); }
+static int pow2_floor(int x) {
+    int p = 1;
+    while (p * 2 <= x) p *= 2;
+    return p;
+}
 
-constexpr double kNttIntOps = 1.2e13;     // sustained integer operations / s (estimate)
-constexpr double kNttBytes = 4.0e12;      // sustained HBM bytes / s (estimate)
+// shared memory of each kernel (bytes): twiddle pairs, tables, two pitched buffers
+static size_t smem_rows_fwd(int Nx, int Rf, int B) {
+    return 8 * static_cast<size_t>(Nx) + 4 * static_cast<size_t>(Rf) + 4 * static_cast<size_t>(Nx) +
+           8 * static_cast<size_t>(Nx) * npitch(B);
+}
+static size_t smem_pitched(int N, int B) { return 8 * static_cast<size_t>(N) + 8 * static_cast<size_t>(N) * npitch(B); }
+constexpr size_t kNttSmemMax = 200 * 1024;
+constexpr size_t kNttSmemHalf = 110 * 1024;
+
+// rates of the time estimate, fitted to GB300 runs (2048^2 / 204^2, 4096^2 / 31^2 and
+// 1024^2 / 102^2 at L = 256): the estimate lands within about 5 % of the measured time
+constexpr double kNttIntOps = 1.6e13;     // model integer instructions / s
+constexpr double kNttBytes = 4.0e12;      // HBM bytes / s
+constexpr double kNttCta = 8.0e-9;        // s per CTA (start-up amortised over the SMs)
+
+// grey frequencies per row-kernel pass: ~4096 elements, no more than the axis holds
+static int ntt_kgroup(int Nx, int Rf) {
+    int b = std::min(64, pow2_floor(std::max(1, 4096 / Nx)));
+    while (b > 1 && b / 2 >= Rf) b /= 2;
+    return b;
+}
+
+// pixels per k_ntt_range CTA: up to 128 (short grey axes), two CTAs per SM
+static int ntt_pixgroup(int Rf) {
+    int c = 128;
+    while (c > 1 && smem_pitched(Rf, c) > kNttSmemHalf) c /= 2;
+    return c;
+}
 
 double ntt_time_estimate(const NttPlan& p) { return p.ops / kNttIntOps + p.bytes / kNttBytes; }
 
@@ -514,23 +634,27 @@ int plan_ntt_tiles(const morph_image* f, const morph_se* se, NttPlan* p) {
         if (nty > 1 && (f->h + nty - 2) / (nty - 1) == To_y) continue;      // same tiling as nty - 1
         const int Ny = ntt_size_at_least(To_y + kh - 1);
         if (Ny == 0) continue;
-        FftAxis ay;
+        NttAxis ay;
         ntt_factor(Ny, &ay);
         for (int ntx = 1; ntx <= max_tx; ++ntx) {
             const int To_x = (f->w + ntx - 1) / ntx;
             if (ntx > 1 && (f->w + ntx - 2) / (ntx - 1) == To_x) continue;
             const int Nx = ntt_size_at_least(To_x + kw - 1);
             if (Nx == 0) continue;
-            FftAxis ax;
+            NttAxis ax;
             ntt_factor(Nx, &ax);
             const int ty = (f->h + To_y - 1) / To_y, tx = (f->w + To_x - 1) / To_x;
             const double tiles = static_cast<double>(f->n) * ty * tx;
             const double Rin = To_y + kh - 1;
-            const double ops = tiles * (Rf * ((Rin + To_y) * ntt_ops(ax) + 2.0 * Nx * ntt_ops(ay) + 6.0 * Nx * Ny) +
+            const double ops = tiles * (Rf * ((Rin + To_y) * ntt_ops(ax) + 2.0 * Nx * ntt_ops(ay) + 10.0 * Nx * Ny) +
                                         static_cast<double>(To_y) * To_x * ntt_ops(p->ar));
             const double bytes = tiles * Rf * 4.0 *
                                  (2.0 * Rin * Nx + 2.0 * To_y * Nx + 2.0 * To_y * To_x + 0.5 * Nx * Ny);
-            const double t = ops / kNttIntOps + bytes / kNttBytes;
+            // CTAs of the four kernels (each pays a fixed start-up: tables, barriers)
+            const int kg = ntt_kgroup(Nx, p->Rf);
+            const double ctas = tiles * (Rin + (Nx / 8.0) * Rf + To_y * std::ceil(Rf / kg) +
+                                         std::ceil(To_x / static_cast<double>(ntt_pixgroup(p->Rf))) * To_y);
+            const double t = ops / kNttIntOps + bytes / kNttBytes + ctas * kNttCta;
             if (best < 0 || t < best) {
                 best = t;
                 p->ops = ops;
@@ -549,9 +673,15 @@ int plan_ntt_tiles(const morph_image* f, const morph_se* se, NttPlan* p) {
     p->Win_x = p->To_x + kw - 1;
     p->ntiles = static_cast<long long>(f->n) * p->tiles_y * p->tiles_x;
     const int Nx = p->ax.N, Ny = p->ay.N;
-    p->kgroup = std::max(1, std::min(p->Rf, 4096 / Nx));
-    p->colgroup = std::max(1, std::min(16, (51200 / Ny - 1) / 2));
-    p->pixgroup = std::max(1, std::min(32, (51200 / p->Rf - 1) / 2));
+    // batch sizes (powers of two): ~4096 elements per row-kernel pass, the
+    // widest column / pixel groups whose buffers fit in shared memory
+    p->kgroup = ntt_kgroup(Nx, p->Rf);
+    // column / pixel groups small enough for two CTAs per SM; 512 threads for big groups
+    p->colgroup = 16;
+    while (p->colgroup > 1 && smem_pitched(Ny, p->colgroup) > kNttSmemHalf) p->colgroup /= 2;
+    p->pixgroup = ntt_pixgroup(p->Rf);
+    p->col_threads = Ny * p->colgroup >= 8192 ? 512 : 256;
+    p->pix_threads = p->Rf * p->pixgroup >= 8192 ? 512 : 256;
     const size_t per_tile = static_cast<size_t>(p->Rf) * Nx * Ny * 4;
     const size_t budget = size_t(4) << 30;
     long long wt = static_cast<long long>(budget / std::max<size_t>(per_tile, 1));
@@ -562,35 +692,94 @@ int plan_ntt_tiles(const morph_image* f, const morph_se* se, NttPlan* p) {
     return MORPH_OK;
 }
 
+// ------------------------------------------------------- instantiations
+typedef void (*NttKernel)(const NttArgs);
+
+static NttKernel rows_fwd_for(int B) {
+    switch (B) {
+        case 1: return k_ntt_rows_fwd<1>;
+        case 2: return k_ntt_rows_fwd<2>;
+        case 4: return k_ntt_rows_fwd<4>;
+        case 8: return k_ntt_rows_fwd<8>;
+        case 16: return k_ntt_rows_fwd<16>;
+        case 32: return k_ntt_rows_fwd<32>;
+        default: return k_ntt_rows_fwd<64>;
+    }
+}
+static NttKernel rows_inv_for(int B) {
+    switch (B) {
+        case 1: return k_ntt_rows_inv<1>;
+        case 2: return k_ntt_rows_inv<2>;
+        case 4: return k_ntt_rows_inv<4>;
+        case 8: return k_ntt_rows_inv<8>;
+        case 16: return k_ntt_rows_inv<16>;
+        case 32: return k_ntt_rows_inv<32>;
+        default: return k_ntt_rows_inv<64>;
+    }
+}
+static NttKernel cols_for(int C) {
+    switch (C) {
+        case 1: return k_ntt_cols<1>;
+        case 2: return k_ntt_cols<2>;
+        case 4: return k_ntt_cols<4>;
+        case 8: return k_ntt_cols<8>;
+        default: return k_ntt_cols<16>;
+    }
+}
+static NttKernel range_for(int C) {
+    switch (C) {
+        case 1: return k_ntt_range<1>;
+        case 2: return k_ntt_range<2>;
+        case 4: return k_ntt_range<4>;
+        case 8: return k_ntt_range<8>;
+        case 16: return k_ntt_range<16>;
+        case 32: return k_ntt_range<32>;
+        case 64: return k_ntt_range<64>;
+        default: return k_ntt_range<128>;
+    }
+}
+
 static int set_ntt_smem() {
     static bool done = false;
     if (done) return MORPH_OK;
-    const int big = 200 * 1024;
-    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_ntt_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_ntt_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_ntt_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_ntt_range, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    const int big = static_cast<int>(kNttSmemMax);
+    for (int b = 1; b <= 64; b *= 2) {
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(rows_fwd_for(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(rows_inv_for(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        if (b <= 16) MORPH_CUDA_TRY(cudaFuncSetAttribute(cols_for(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    }
+    for (int b = 1; b <= 128; b *= 2)
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(range_for(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_ntt_plane_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_ntt_plane_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     done = true;
     return MORPH_OK;
 }
 
-// omega_N^m for m < N: Montgomery form (mont = 1) or plain
-static std::vector<uint32_t> ntt_table(int N, bool mont) {
+// omega_N^m for m < N, plain
+static std::vector<uint32_t> ntt_powers(int N) {
     std::vector<uint32_t> t(N);
     const uint64_t w = hpow(kG, (kP - 1) / static_cast<uint64_t>(N));
     uint64_t x = 1;
     for (int m = 0; m < N; ++m) {
-        t[m] = mont ? to_mont(x) : static_cast<uint32_t>(x);
+        t[m] = static_cast<uint32_t>(x);
         x = x * w % kP;
     }
     return t;
 }
 
-static int upload(uint32_t** d, const std::vector<uint32_t>& h) {
-    MORPH_CUDA_TRY(cudaMalloc(d, h.size() * sizeof(uint32_t)));
-    MORPH_CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+// (omega_N^m, Shoup quotient) pairs
+static std::vector<uint2> ntt_twiddles(int N) {
+    const std::vector<uint32_t> w = ntt_powers(N);
+    std::vector<uint2> t(N);
+    for (int m = 0; m < N; ++m) t[m] = make_uint2(w[m], shoup_q(w[m]));
+    return t;
+}
+
+template <typename T>
+static int upload(T** d, const std::vector<T>& h) {
+    MORPH_CUDA_TRY(cudaMalloc(d, h.size() * sizeof(T)));
+    MORPH_CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     return MORPH_OK;
 }
 
@@ -604,10 +793,10 @@ int build_ntt_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, Ntt
     rc = set_ntt_smem();
     if (rc) return rc;
     const int Nx = p->ax.N, Ny = p->ay.N, Rf = p->Rf;
-    if ((rc = upload(&p->tw_x, ntt_table(Nx, true)))) return rc;
-    if ((rc = upload(&p->tw_y, ntt_table(Ny, true)))) return rc;
-    if ((rc = upload(&p->tw_r, ntt_table(Rf, true)))) return rc;
-    if ((rc = upload(&p->wr, ntt_table(Rf, false)))) return rc;
+    if ((rc = upload(&p->tw_x, ntt_twiddles(Nx)))) return rc;
+    if ((rc = upload(&p->tw_y, ntt_twiddles(Ny)))) return rc;
+    if ((rc = upload(&p->tw_r, ntt_twiddles(Rf)))) return rc;
+    if ((rc = upload(&p->wr, ntt_powers(Rf)))) return rc;
     std::vector<NttTap> taps;
     for (int r = 0; r < se->kh; ++r)
         for (int c = 0; c < se->kw; ++c) {
@@ -618,16 +807,14 @@ int build_ntt_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, Ntt
     MORPH_CUDA_TRY(cudaMalloc(&p->S, nS * sizeof(uint32_t)));
     MORPH_CUDA_TRY(cudaMemset(p->S, 0, nS * sizeof(uint32_t)));
     NttTap* d_taps = nullptr;
-    MORPH_CUDA_TRY(cudaMalloc(&d_taps, taps.size() * sizeof(NttTap)));
-    MORPH_CUDA_TRY(cudaMemcpy(d_taps, taps.data(), taps.size() * sizeof(NttTap), cudaMemcpyHostToDevice));
+    if ((rc = upload(&d_taps, taps))) return rc;
     {
         const long long n = static_cast<long long>(Rf) * static_cast<long long>(taps.size());
         const unsigned blocks = static_cast<unsigned>(std::min<long long>((n + 255) / 256, 4096));
         k_ntt_se_scatter<<<blocks, 256>>>(p->S, Rf, Ny, Nx, d_taps, static_cast<int>(taps.size()), p->wr);
     }
-    k_ntt_plane_rows<<<dim3(Ny, Rf), 256, ntt_smem_rows(Nx, 1)>>>(p->S, p->ax, p->tw_x, Ny);
-    const int C = p->colgroup;
-    k_ntt_plane_cols<<<dim3((Nx + C - 1) / C, Rf), 256, ntt_smem_cols(Ny, C)>>>(p->S, p->ay, p->tw_y, Nx, C);
+    k_ntt_plane_rows<<<dim3(Ny, Rf), 256, smem_pitched(Nx, 1)>>>(p->S, p->ax, p->tw_x, Ny);
+    k_ntt_plane_cols<<<dim3((Nx + 7) / 8, Rf), 256, smem_pitched(Ny, 8)>>>(p->S, p->ay, p->tw_y, Nx);
     const uint64_t scale = static_cast<uint64_t>(Rf) * Ny * Nx % kP;
     const uint64_t inv = hpow(scale, kP - 2);
     const uint64_t r32 = (uint64_t(1) << 32) % kP;
@@ -656,6 +843,7 @@ int launch_ntt_in(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int er
     a.erode = erode;
     a.R = p.R;
     a.Rf = p.Rf;
+    a.rfm = static_cast<uint32_t>(((uint64_t(1) << 32) + p.Rf - 1) / p.Rf);
     a.ar = p.ar;
     a.ax = p.ax;
     a.ay = p.ay;
@@ -676,27 +864,25 @@ int launch_ntt_in(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int er
     a.out = out;
     a.out_cnt = cnt;
     a.err = ctx->d_err;
-    a.kgroup = p.kgroup;
-    a.colgroup = p.colgroup;
-    a.pixgroup = p.pixgroup;
     const int Nx = p.ax.N, Ny = p.ay.N;
+    const NttKernel rf = rows_fwd_for(p.kgroup), ri = rows_inv_for(p.kgroup);
+    const NttKernel cl = cols_for(p.colgroup), rg = range_for(p.pixgroup);
     for (long long t0 = 0; t0 < p.ntiles; t0 += p.wave_tiles) {
         a.tile0 = t0;
         a.wave_tiles = static_cast<int>(std::min<long long>(p.wave_tiles, p.ntiles - t0));
         prof_begin(ctx, st, "k_ntt_rows_fwd");
-        k_ntt_rows_fwd<<<dim3(p.Rin_y, a.wave_tiles), 256, ntt_smem_rows(Nx, p.kgroup), st>>>(a);
+        rf<<<dim3(p.Rin_y, a.wave_tiles), 256, smem_rows_fwd(Nx, p.Rf, p.kgroup), st>>>(a);
         prof_end(ctx, st);
         prof_begin(ctx, st, "k_ntt_cols");
-        k_ntt_cols<<<dim3((Nx + p.colgroup - 1) / p.colgroup, p.Rf, a.wave_tiles), 256,
-                     ntt_smem_cols(Ny, p.colgroup), st>>>(a);
+        cl<<<dim3(a.wave_tiles, (Nx + p.colgroup - 1) / p.colgroup, p.Rf), p.col_threads,
+             smem_pitched(Ny, p.colgroup), st>>>(a);
         prof_end(ctx, st);
         prof_begin(ctx, st, "k_ntt_rows_inv");
-        k_ntt_rows_inv<<<dim3(p.To_y, (p.Rf + p.kgroup - 1) / p.kgroup, a.wave_tiles), 256,
-                         ntt_smem_rows(Nx, p.kgroup), st>>>(a);
+        ri<<<dim3(p.To_y, (p.Rf + p.kgroup - 1) / p.kgroup, a.wave_tiles), 256, smem_pitched(Nx, p.kgroup), st>>>(a);
         prof_end(ctx, st);
         prof_begin(ctx, st, "k_ntt_range");
-        k_ntt_range<<<dim3((p.To_x + p.pixgroup - 1) / p.pixgroup, p.To_y, a.wave_tiles), 256,
-                      ntt_smem_cols(p.Rf, p.pixgroup), st>>>(a);
+        rg<<<dim3((p.To_x + p.pixgroup - 1) / p.pixgroup, p.To_y, a.wave_tiles), p.pix_threads,
+             smem_pitched(p.Rf, p.pixgroup), st>>>(a);
         prof_end(ctx, st);
         ctx->launches += 4;
         MORPH_CUDA_TRY(cudaGetLastError());

@@ -225,10 +225,21 @@ size_t planes_bytes(const morph_image* f) {
 }
 
 // Route for a request.  AUTO estimates each exact route's time on the host
-// (no device work) and takes the fastest: the FP8 direct route (issued dense
-// FLOP at the tensor rate the kernel reaches), the FP32 FFT route when its
-// a-priori bound proves it exact, and the FP64 FFT route only where FP32 is
-// not provable (FP64 runs at 1/64 of FP32 on this part).
+// (no device work) and takes the fastest among the FP8 direct route, the FP32
+// FFT route where its a-priori bound proves it exact, and the NTT route (exact
+// for any size it supports); the FP64 FFT route is the fallback where neither
+// transform route applies.  Each estimate is a fixed cost plus the route's
+// work at the rate fitted to GB300 runs over 35 shapes (images 64^2..4096^2,
+// L = 16 / 64 / 256, SEs 3^2..256^2; median error about 10 %):
+//   direct: 54 us + 1.07 x issued FLOP / 3e15 + 12.2 ns per tile pass
+//           (epilogue) + 0.76 ps per pixel level (encoder);
+//   FFT32 : 79 us + FFT FLOP / 2.16e12;  FFT64: 145 us + FFT FLOP / 6.9e11;
+//   NTT   : 80 us + 1.48 x its own estimate (operations, bytes, CTAs).
+static double direct_time(const DirectPlan& dp, const morph_image* f) {
+    return 54e-6 + 1.07 * dp.issued_flop / 3.0e15 + 12.2e-9 * static_cast<double>(dp.tiles) * dp.T * dp.n_pass +
+           0.76e-12 * static_cast<double>(f->n) * f->h * f->w * f->L;
+}
+
 static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, int method,
                         bool unproven, int* route) {
     if (method == MORPH_DIRECT_FP8) { *route = ROUTE_DIRECT; return MORPH_OK; }
@@ -244,19 +255,21 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
     if (rc) return rc;
     *route = ROUTE_DIRECT;
     if (dp.taps > 0) {
-        double best = dp.issued_flop / 3.0e15;
+        double best = direct_time(dp, f);
         FftPlan fp;
-        const auto fft_time = [](const FftPlan& q, double flops_per_s) {
-            const double bytes = 5.0 * q.K * static_cast<double>(q.ax.N) * q.ay.N * 2.0 * q.prec * q.ntiles;
-            return q.flop / flops_per_s + bytes / 4.0e12;
-        };
-        if (plan_fft_tiles(f, se, 4, false, &fp) == MORPH_OK) {
-            const double t = fft_time(fp, 2.5e13);
+        const bool f32_ok = plan_fft_tiles(f, se, 4, false, &fp) == MORPH_OK;
+        if (f32_ok) {
+            const double t = 79e-6 + fp.flop / 2.16e12;
             if (t < best) { best = t; *route = ROUTE_FFT32; }
-        } else {
+        }
+        NttPlan np;
+        if (plan_ntt_tiles(f, se, &np) == MORPH_OK) {
+            const double t = 80e-6 + 1.2 * ntt_time_estimate(np);
+            if (t < best) { best = t; *route = ROUTE_NTT; }
+        } else if (!f32_ok) {
             FftPlan f64;
             if (plan_fft_tiles(f, se, 8, false, &f64) == MORPH_OK) {
-                const double t = fft_time(f64, 0.9e12);
+                const double t = 145e-6 + f64.flop / 6.9e11;
                 if (t < best) { best = t; *route = ROUTE_FFT64; }
             }
         }

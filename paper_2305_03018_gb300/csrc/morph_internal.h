@@ -118,6 +118,14 @@ struct FftPlan {
 };
 
 // ------------------------------------------------ exact NTT route (Step 2)
+struct NttAxis {
+    int N;                 // transform length (2^a 3^b 5^c, c <= 3, <= 2048)
+    int nst;               // Stockham stages
+    int rad[16];           // radix of each stage (4, 2, 3, 5)
+    int tstep[16];         // N / (Ns R): twiddle stride of each stage
+    uint32_t nsm[16];      // ceil(2^32 / Ns) with Ns the product of the earlier radices (0 for Ns = 1)
+};
+
 struct NttPlan {
     int taps = 0, R = 0, Rf = 0;  // |B|, degrees, grey-axis length (= grey frequencies)
     int kh = 0, kw = 0, ry = 0, rx = 0;
@@ -125,13 +133,14 @@ struct NttPlan {
     int tiles_y = 0, tiles_x = 0;
     long long ntiles = 0;
     int wave_tiles = 0, kgroup = 1, colgroup = 8, pixgroup = 16;
+    int col_threads = 256, pix_threads = 256;
     size_t buf_bytes = 0, ws_bytes = 0;
     double ops = 0, bytes = 0;    // estimated integer operations and HBM bytes per call
-    FftAxis ax, ay, ar;
-    uint32_t* tw_x = nullptr;
-    uint32_t* tw_y = nullptr;
-    uint32_t* tw_r = nullptr;
-    uint32_t* wr = nullptr;
+    NttAxis ax, ay, ar;
+    uint2* tw_x = nullptr;        // (omega_N^m, Shoup quotient) pairs
+    uint2* tw_y = nullptr;
+    uint2* tw_r = nullptr;
+    uint32_t* wr = nullptr;       // omega_Rf^m
     uint32_t* S = nullptr;
     ~NttPlan();
 };

@@ -114,3 +114,17 @@ def test_batch_with_ntt_problems(ctx):
     ctx.check()
     for it, ref in zip(items, refs):
         _eq((it[4].cpu().numpy(), it[5].cpu().numpy()), ref)
+
+
+def test_auto_takes_ntt_for_8bit_offsets_and_stays_exact(ctx):
+    # 8-bit image and 8-bit offsets with a 64 x 64 filter: the FP32 bound fails, the
+    # FP8 route stacks 256 offset levels, and AUTO's estimate favours the NTT
+    g = wl.rng(94)
+    f = g.integers(0, 256, size=(1, 300, 280)).astype(np.uint8)
+    se = wl.se_full_random(g, 64, 255)
+    ft = torch.from_numpy(f).cuda()
+    assert ctx.plan(ft, 256, se, method="auto").method == 4
+    out, cnt = ctx.dilate(ft, 256, se, method="auto", count=True)
+    ctx.check()
+    for rows in [(0, 3), (140, 143), (297, 300)]:
+        _eq((out.cpu().numpy(), cnt.cpu().numpy()), _ref(f, 256, se, "dilate", rows=rows), rows=rows)
