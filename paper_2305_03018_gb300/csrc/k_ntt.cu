@@ -228,6 +228,7 @@ struct NttArgs {
     int32_t* out;
     int32_t* out_cnt;
     unsigned int* err;
+    int kper;                       // grey frequencies per CTA of k_ntt_rows_fwd (multiple of its batch)
 };
 
 __device__ __forceinline__ int ntt_load_px(const void* src, int dtype, long long idx) {
@@ -248,7 +249,8 @@ __device__ __forceinline__ void ntt_copy_tw(uint2* dst, const uint2* src, int n)
     for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = src[j];
 }
 
-// grid (Rin_y, wave_tiles): input row rho of tile tl, every grey frequency, B at a time
+// grid (Rin_y, wave_tiles, ceil(Rf / kper)): input row rho of tile tl, grey
+// frequencies [z kper, (z + 1) kper), B at a time
 template <int B>
 __global__ void __launch_bounds__(256) k_ntt_rows_fwd(const NttArgs a) {
     constexpr int PB = npitch(B);
@@ -280,7 +282,8 @@ __global__ void __launch_bounds__(256) k_ntt_rows_fwd(const NttArgs a) {
     __syncthreads();
     const long long plane = static_cast<long long>(a.ay.N) * Nx;
     uint32_t* dst = a.buf + static_cast<long long>(tl) * Rf * plane + static_cast<long long>(rho) * Nx;
-    for (int k0 = 0; k0 < Rf; k0 += B) {
+    const int kend = min(Rf, static_cast<int>(blockIdx.z + 1) * a.kper);
+    for (int k0 = blockIdx.z * a.kper; k0 < kend; k0 += B) {
         for (int t = threadIdx.x; t < B * Nx; t += blockDim.x) {
             const int c = t & (B - 1), p = t >> ilog2c(B);
             const int l = lev[p];
@@ -871,7 +874,14 @@ int launch_ntt_in(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int er
         a.tile0 = t0;
         a.wave_tiles = static_cast<int>(std::min<long long>(p.wave_tiles, p.ntiles - t0));
         prof_begin(ctx, st, "k_ntt_rows_fwd");
-        rf<<<dim3(p.Rin_y, a.wave_tiles), 256, smem_rows_fwd(Nx, p.Rf, p.kgroup), st>>>(a);
+        // split the grey frequencies over CTAs when rows x tiles alone would leave SMs idle
+        const int groups = (p.Rf + p.kgroup - 1) / p.kgroup;
+        const long long rows = static_cast<long long>(p.Rin_y) * a.wave_tiles;
+        const int ksplit = static_cast<int>(std::max<long long>(
+            1, std::min<long long>(groups, (8LL * ctx->num_sms + rows - 1) / rows)));
+        a.kper = ((groups + ksplit - 1) / ksplit) * p.kgroup;
+        rf<<<dim3(p.Rin_y, a.wave_tiles, (p.Rf + a.kper - 1) / a.kper), 256, smem_rows_fwd(Nx, p.Rf, p.kgroup),
+             st>>>(a);
         prof_end(ctx, st);
         prof_begin(ctx, st, "k_ntt_cols");
         cl<<<dim3(a.wave_tiles, (Nx + p.colgroup - 1) / p.colgroup, p.Rf), p.col_threads,
