@@ -99,7 +99,11 @@ struct NttConst {
     uint32_t w, q;
 };
 constexpr NttConst nconst(uint64_t c) { return NttConst{static_cast<uint32_t>(c), shoup_q(c)}; }
+constexpr uint64_t kW16 = npow(kG, (kP - 1) / 16);
 constexpr NttConst kW3c = nconst(kW3), kW4c = nconst(kW4);
+// omega_16^m for the products m = n2 k1 (n2, k1 in 1..3) inside a radix-16 butterfly
+constexpr NttConst kW16_1c = nconst(kW16), kW16_2c = nconst(npow(kW16, 2)), kW16_3c = nconst(npow(kW16, 3));
+constexpr NttConst kW16_4c = nconst(npow(kW16, 4)), kW16_6c = nconst(npow(kW16, 6)), kW16_9c = nconst(npow(kW16, 9));
 constexpr NttConst kC1c = nconst(kC1), kC2c = nconst(kC2), kS1c = nconst(kS1), kS2c = nconst(kS2);
 #define NTT_K(x) x##c.w, x##c.q
 
@@ -145,6 +149,36 @@ __device__ __forceinline__ void ndft5(uint32_t* v) {
     v[3] = lsub(A2, B2);
 }
 
+// Radix 16 as 4 x 4: with n = 4 n1 + n2 and k = k1 + 4 k2,
+// y_k = sum_n2 omega_16^(n2 k1) omega_4^(n2 k2) sum_n1 v_(4 n1 + n2) omega_4^(n1 k1):
+// four radix-4 DFTs over n1, the nine twiddles omega_16^(n2 k1), four radix-4 DFTs over n2.
+__device__ __forceinline__ void ndft16(uint32_t* v) {
+    uint32_t u[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        uint32_t w[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+        ndft4(w);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) u[n2][k1] = w[k1];
+    }
+    u[1][1] = lmul(u[1][1], NTT_K(kW16_1));
+    u[1][2] = lmul(u[1][2], NTT_K(kW16_2));
+    u[1][3] = lmul(u[1][3], NTT_K(kW16_3));
+    u[2][1] = lmul(u[2][1], NTT_K(kW16_2));
+    u[2][2] = lmul(u[2][2], NTT_K(kW16_4));
+    u[2][3] = lmul(u[2][3], NTT_K(kW16_6));
+    u[3][1] = lmul(u[3][1], NTT_K(kW16_3));
+    u[3][2] = lmul(u[3][2], NTT_K(kW16_6));
+    u[3][3] = lmul(u[3][3], NTT_K(kW16_9));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        uint32_t w[4] = {u[0][k1], u[1][k1], u[2][k1], u[3][k1]};
+        ndft4(w);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = w[k2];
+    }
+}
+
 constexpr int ilog2c(int b) { return b <= 1 ? 0 : 1 + ilog2c(b / 2); }
 // element p of transform c of a batch of B lives at p * pitch(B) + c; the odd
 // pitch keeps column reads (fixed c, consecutive p) free of bank conflicts
@@ -178,6 +212,7 @@ __device__ __forceinline__ void ntt_stage(const uint32_t* __restrict__ x, uint32
         if (R == 3) ndft3(v);
         if (R == 4) ndft4(v);
         if (R == 5) ndft5(v);
+        if (R == 16) ndft16(v);
         const int d = g * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) y[(d + r * Ns) * PB + c] = v[r];
@@ -187,11 +222,12 @@ __device__ __forceinline__ void ntt_stage(const uint32_t* __restrict__ x, uint32
 // Forward NTT of B interleaved transforms in a (scratch b); returns the buffer
 // holding the result.  Block-wide; ends with a barrier.
 template <int B>
-__device__ uint32_t* ntt_block(uint32_t* a, uint32_t* b, const NttAxis& ax, const uint2* tw) {
+__device__ __forceinline__ uint32_t* ntt_block(uint32_t* a, uint32_t* b, const NttAxis& ax, const uint2* tw) {
     int Ns = 1;
     for (int s = 0; s < ax.nst; ++s) {
         const int R = ax.rad[s];
-        if (R == 4) ntt_stage<4, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
+        if (R == 16) ntt_stage<16, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
+        else if (R == 4) ntt_stage<4, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
         else if (R == 2) ntt_stage<2, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
         else if (R == 3) ntt_stage<3, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
         else ntt_stage<5, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
@@ -525,18 +561,20 @@ NttPlan::~NttPlan() {
 
 static uint64_t hpow(uint64_t b, uint64_t e) { return npow(b, e); }
 
-// N = 2^a 3^b 5^c with c <= 3 (P - 1 = 2^14 3^6 5^3), stages 4, 2, 3, 5, with
+// N = 2^a 3^b 5^c with c <= 3 (P - 1 = 2^13 3^6 5^3), stages 16, 4, 2, 3, 5, with
 // each stage's twiddle stride and the division magic for Ns
 static bool ntt_factor(int N, NttAxis* ax) {
     if (N < 1 || N > kNttMaxN) return false;
     ax->N = N;
     ax->nst = 0;
-    int m = N, f4 = 0, f2 = 0, f3 = 0, f5 = 0;
+    int m = N, f16 = 0, f4 = 0, f2 = 0, f3 = 0, f5 = 0;
+    while (m % 16 == 0) { m /= 16; ++f16; }
     while (m % 4 == 0) { m /= 4; ++f4; }
     while (m % 2 == 0) { m /= 2; ++f2; }
     while (m % 3 == 0) { m /= 3; ++f3; }
     while (m % 5 == 0) { m /= 5; ++f5; }
-    if (m != 1 || f5 > 3 || f3 > 6 || f4 + f2 + f3 + f5 > 16) return false;
+    if (m != 1 || f5 > 3 || f3 > 6 || f16 + f4 + f2 + f3 + f5 > 16) return false;
+    for (int i = 0; i < f16; ++i) ax->rad[ax->nst++] = 16;
     for (int i = 0; i < f4; ++i) ax->rad[ax->nst++] = 4;
     for (int i = 0; i < f2; ++i) ax->rad[ax->nst++] = 2;
     for (int i = 0; i < f3; ++i) ax->rad[ax->nst++] = 3;
@@ -569,7 +607,7 @@ static double ntt_ops(const NttAxis& a) {
     double per = 0;
     for (int s = 0; s < a.nst; ++s) {
         const int r = a.rad[s];
-        per += r == 2 ? 6.0 : r == 4 ? 11.0 : r == 3 ? 12.0 : 24.0;
+        per += r == 2 ? 6.0 : r == 4 ? 11.0 : r == 16 ? 16.0 : r == 3 ? 12.0 : 24.0;
     }
     return per * a.N;
 }

@@ -121,7 +121,7 @@ struct FftPlan {
 struct NttAxis {
     int N;                 // transform length (2^a 3^b 5^c, c <= 3, <= 2048)
     int nst;               // Stockham stages
-    int rad[16];           // radix of each stage (4, 2, 3, 5)
+    int rad[16];           // radix of each stage (16, 4, 2, 3, 5)
     int tstep[16];         // N / (Ns R): twiddle stride of each stage
     uint32_t nsm[16];      // ceil(2^32 / Ns) with Ns the product of the earlier radices (0 for Ns = 1)
 };
