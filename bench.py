@@ -47,8 +47,13 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FFT-form comparison")
     ap.add_argument("--cpu-rows", type=int, default=48, help="oracle sample: rows per operation")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "x1", "x2"], default="c2",
-                    help="c2 (default) is the headline workload; the others time the remaining configurations")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "x1", "x2", "one"], default="c2",
+                    help="c2 (default) is the headline workload; the others time the remaining configurations; "
+                         "'one' times a single dilation of the sweeps' recipe (--image, --levels, --filter, --method)")
+    ap.add_argument("--image", type=int, default=512, help="one: image side")
+    ap.add_argument("--levels", type=int, default=256, help="one: grey levels L (image and offsets in 0..L-1)")
+    ap.add_argument("--filter", type=int, default=64, help="one: full-support filter side")
+    ap.add_argument("--method", default="auto", help="one: auto | direct_fp8 | fft_f32 | fft_f64 | ntt")
     return ap.parse_args()
 
 
@@ -605,11 +610,54 @@ def run_sweep(args, ws, rank, local):
     return 0
 
 
+def run_one(args, ws, rank, local):
+    """One dilation of an n x n randint image by a k x k full-support randint
+    filter (the recipe of the paper's runtime experiments, Sec. 4.1) with one
+    method: warm-up, then `steps` timed calls, each with its kernel times."""
+    import torch
+
+    from paper_2305_03018_gb300 import workloads as wl
+    from paper_2305_03018_gb300.morph import get_context
+    torch.cuda.set_device(local)
+    ctx = get_context(local)
+    n, L, k = args.image, args.levels, args.filter
+    g = wl.rng(1000 * n + k + (4 if L <= 16 else 8))
+    f = torch.from_numpy(wl.uniform_image(g, (1, n, n), L)).cuda()
+    se = wl.se_full_random(g, k, L - 1)
+    info = ctx.plan(f, L, se, method=args.method)
+    out = torch.empty((1, n, n), dtype=torch.int32, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        ctx.dilate(f, L, se, method=args.method, out=out)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(max(1, args.steps)):
+        ctx.dilate(f, L, se, method=args.method, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    kt = ctx.profile_read()
+    ctx.profile(False)
+    ctx.check()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    line = {"metric": METRIC, "workload": "one", "unit": "ms per dilation", "value": ms, "steps": args.steps,
+            "config": {"image": n, "L": L, "filter": k, "method": args.method,
+                       "method_used": {1: "direct_fp8", 2: "fft_f32", 3: "fft_f64", 4: "ntt"}.get(info.method),
+                       "fft_nx": info.fft_nx, "fft_ny": info.fft_ny, "tile": [info.tile_h, info.tile_w],
+                       "workspace_bytes": info.workspace_bytes, "est_ops": info.est_flop},
+            "kernel_ms_per_call": {kk: v[1] / max(1, args.steps) for kk, v in kt.items()}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     ws, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload == "one":
+        return run_one(args, ws, rank, local)
     if args.workload in ("x1", "x2"):
         return run_sweep(args, ws, rank, local)
     if args.workload != "c2":

@@ -115,3 +115,40 @@ class MorphErode2d(_MorphLayer):
 
     def forward(self, x):
         return erode(x, self.offset, self.L, self.mask, self.origin)
+
+
+# ------------------------------------------------------------ composites
+# The composite operators (the combinations named in the paper's conclusion)
+# as compositions of the exact layers, so their backward composes through
+# autograd.  The erosion's output lies in [-max b, L-1]; before a second pass
+# it is shifted by max b into the tonal range [0, L + max b) of that pass
+# (the shift has gradient 1), which needs L + max b <= 256.
+
+def _tonal_shift(b, L: int):
+    mb = int(b.detach().round().clamp(min=0).max().item()) if b.numel() else 0
+    if L + mb > 256:
+        raise ValueError(f"composite needs L + max b <= 256 (got {L} + {mb})")
+    return mb
+
+
+def opening(x, b, L: int, mask=None, origin=None):
+    """Differentiable opening (x erode b) dilate b."""
+    mask, origin = _defaults(b, mask, origin)
+    mb = _tonal_shift(b, L)
+    e = _MorphFunction.apply(x, b, int(L), mask, origin, 1)
+    return _MorphFunction.apply(e + mb, b, int(L) + mb, mask, origin, 0) - mb
+
+
+def closing(x, b, L: int, mask=None, origin=None):
+    """Differentiable closing (x dilate b) erode b."""
+    mask, origin = _defaults(b, mask, origin)
+    mb = _tonal_shift(b, L)
+    d = _MorphFunction.apply(x, b, int(L), mask, origin, 0)
+    return _MorphFunction.apply(d, b, int(L) + mb, mask, origin, 1)
+
+
+def gradient(x, b, L: int, mask=None, origin=None):
+    """Differentiable Beucher gradient (x dilate b) - (x erode b)."""
+    mask, origin = _defaults(b, mask, origin)
+    return (_MorphFunction.apply(x, b, int(L), mask, origin, 0) -
+            _MorphFunction.apply(x, b, int(L), mask, origin, 1))
