@@ -23,11 +23,16 @@ struct BwdTap {
     int dy, dx, b, box;   // y = (dy, dx), b(y), box index r * kw + c
 };
 
-__device__ __forceinline__ int load_px(const void* src, int dtype, long long idx) {
-    if (dtype == MORPH_U8) return static_cast<const uint8_t*>(src)[idx];
-    if (dtype == MORPH_U16) return static_cast<const uint16_t*>(src)[idx];
+template <int DT>
+__device__ __forceinline__ int load_px(const void* src, long long idx) {
+    if (DT == MORPH_U8) return static_cast<const uint8_t*>(src)[idx];
+    if (DT == MORPH_U16) return static_cast<const uint16_t*>(src)[idx];
     return static_cast<const int32_t*>(src)[idx];
 }
+
+struct BwdRow {
+    int dy, t0, t1;       // SE row offset and its taps [t0, t1) in the tap list
+};
 
 struct BwdImage {
     const void* f;
@@ -36,71 +41,117 @@ struct BwdImage {
     int sgn;        // +1 dilation, -1 erosion
 };
 
+// q(x) = g(x) / cD(x), or 0 where no tap was valid: the share of the upstream
+// gradient each attaining tap receives (one division per pixel, reused by
+// every tap).
+__global__ void k_bwd_share(const float* __restrict__ g, const int32_t* __restrict__ cD, float* __restrict__ q,
+                            long long total) {
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const int c = cD[x];
+        q[x] = c > 0 ? g[x] / static_cast<float>(c) : 0.f;
+    }
+}
+
+// grid (ceil(w / blockDim), rows): pixel (n, i, j) of image row blockIdx.y
+// (grid-strided over the n h rows) gathers its taps in box order, SE row by
+// SE row.  SGN = +1 dilation, -1 erosion; DT the pixel type.
+template <int SGN, int DT>
 __global__ void __launch_bounds__(256) k_bwd_input(BwdImage im, const int32_t* __restrict__ D,
-                                                   const int32_t* __restrict__ cD, const float* __restrict__ g,
-                                                   const BwdTap* __restrict__ taps, int ntaps,
+                                                   const float* __restrict__ q, const BwdTap* __restrict__ taps,
+                                                   const BwdRow* __restrict__ trows, int nrows,
                                                    float* __restrict__ grad_in) {
-    const long long total = static_cast<long long>(im.n) * im.h * im.w;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int j = static_cast<int>(p % im.w);
-        const long long rr = p / im.w;
-        const int i = static_cast<int>(rr % im.h);
-        const int n = static_cast<int>(rr / im.h);
-        const int fp = load_px(im.f, im.dtype, n * im.batch_stride + i * im.row_stride + j);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= im.w) return;
+    const long long rows = static_cast<long long>(im.n) * im.h;
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int n = static_cast<int>(row / im.h);
+        const int i = static_cast<int>(row - static_cast<long long>(n) * im.h);
+        const int fp = load_px<DT>(im.f, n * im.batch_stride + i * im.row_stride + j);
+        const long long img0 = static_cast<long long>(n) * im.h;
         float acc = 0.f;
-        for (int t = 0; t < ntaps; ++t) {
-            const BwdTap tp = taps[t];
-            const int xi = i + im.sgn * tp.dy, xj = j + im.sgn * tp.dx;
-            if (xi < 0 || xi >= im.h || xj < 0 || xj >= im.w) continue;
-            const long long x = (static_cast<long long>(n) * im.h + xi) * im.w + xj;
-            if (fp + im.sgn * tp.b == D[x]) {
-                const int c = cD[x];
-                if (c > 0) acc += g[x] / static_cast<float>(c);
+        for (int rr = 0; rr < nrows; ++rr) {
+            const BwdRow R = trows[rr];
+            const int xi = i + SGN * R.dy;
+            if (xi < 0 || xi >= im.h) continue;
+            const int32_t* Dr = D + (img0 + xi) * im.w;
+            const float* qr = q + (img0 + xi) * im.w;
+            for (int t = R.t0; t < R.t1; ++t) {
+                const BwdTap tp = taps[t];
+                const int xj = j + SGN * tp.dx;
+                if (static_cast<unsigned>(xj) >= static_cast<unsigned>(im.w)) continue;
+                if (fp + SGN * tp.b == Dr[xj]) acc += qr[xj];
             }
         }
-        grad_in[p] = acc;
+        grad_in[row * im.w + j] = acc;
     }
 }
 
 constexpr int kSeChunk = 8192;      // pixels per partial sum
 constexpr int kSeThreads = 256;
+constexpr int kSeTaps = 8;          // taps per CTA of k_bwd_se_partial (D and q loaded once for all)
 
-// partial[t][chunk] = sum over the chunk's pixels x of the tap-t terms, by a fixed tree.
+struct SeChunks {
+    int CB, RB;              // chunk = RB rows x CB columns of one image (RB CB <= kSeChunk)
+    int cx, cy;              // chunks across, down
+    uint32_t cbm;            // ceil(2^32 / CB): k / CB for k < kSeChunk
+};
+
+// partial[t][chunk] = sum over the chunk's pixels x of the tap-t terms, each
+// thread summing its pixels in order, then a fixed warp and block tree.
+// grid (nchunks, ceil(ntaps / kSeTaps)).
+template <int SGN, int DT>
 __global__ void __launch_bounds__(kSeThreads) k_bwd_se_partial(BwdImage im, const int32_t* __restrict__ D,
-                                                               const int32_t* __restrict__ cD,
-                                                               const float* __restrict__ g,
-                                                               const BwdTap* __restrict__ taps, int nchunks,
+                                                               const float* __restrict__ q,
+                                                               const BwdTap* __restrict__ taps, int ntaps,
+                                                               SeChunks ch, int nchunks,
                                                                float* __restrict__ partial) {
     const int chunk = blockIdx.x;
-    const int t = blockIdx.y;
-    const BwdTap tp = taps[t];
-    const long long total = static_cast<long long>(im.n) * im.h * im.w;
-    const long long x0 = static_cast<long long>(chunk) * kSeChunk;
-    float acc = 0.f;
-    for (int k = threadIdx.x; k < kSeChunk; k += kSeThreads) {
-        const long long x = x0 + k;
-        if (x >= total) break;
-        const int j = static_cast<int>(x % im.w);
-        const long long rr = x / im.w;
-        const int i = static_cast<int>(rr % im.h);
-        const int n = static_cast<int>(rr / im.h);
-        const int si = i - im.sgn * tp.dy, sj = j - im.sgn * tp.dx;
-        if (si < 0 || si >= im.h || sj < 0 || sj >= im.w) continue;
-        const int fs = load_px(im.f, im.dtype, n * im.batch_stride + si * im.row_stride + sj);
-        if (fs + im.sgn * tp.b == D[x]) {
-            const int c = cD[x];
-            if (c > 0) acc += g[x] / static_cast<float>(c);
+    const int t0 = blockIdx.y * kSeTaps;
+    const int nt = min(kSeTaps, ntaps - t0);
+    const int cxi = chunk % ch.cx;
+    const int rest = chunk / ch.cx;
+    const int cyi = rest % ch.cy;
+    const int n = rest / ch.cy;
+    const int i0 = cyi * ch.RB, j0 = cxi * ch.CB;
+    BwdTap tp[kSeTaps];
+#pragma unroll
+    for (int u = 0; u < kSeTaps; ++u) tp[u] = taps[t0 + (u < nt ? u : 0)];
+    float acc[kSeTaps];
+#pragma unroll
+    for (int u = 0; u < kSeTaps; ++u) acc[u] = 0.f;
+    const long long img0 = static_cast<long long>(n) * im.h;
+    for (int k = threadIdx.x; k < ch.RB * ch.CB; k += kSeThreads) {
+        const int r = ch.CB == 1 ? k : static_cast<int>(__umulhi(static_cast<uint32_t>(k), ch.cbm));   // k / CB
+        const int i = i0 + r, j = j0 + (k - r * ch.CB);
+        if (i >= im.h) break;
+        if (j >= im.w) continue;
+        const long long x = (img0 + i) * im.w + j;
+        const int dx = D[x];
+        const float qx = q[x];
+#pragma unroll
+        for (int u = 0; u < kSeTaps; ++u) {
+            if (u >= nt) break;
+            const int si = i - SGN * tp[u].dy, sj = j - SGN * tp[u].dx;
+            if (static_cast<unsigned>(si) >= static_cast<unsigned>(im.h) ||
+                static_cast<unsigned>(sj) >= static_cast<unsigned>(im.w))
+                continue;
+            const int fs = load_px<DT>(im.f, n * im.batch_stride + si * im.row_stride + sj);
+            if (fs + SGN * tp[u].b == dx) acc[u] += qx;
         }
     }
-    __shared__ float red[kSeThreads / 32];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __shared__ float red[kSeTaps][kSeThreads / 32];
+#pragma unroll
+    for (int u = 0; u < kSeTaps; ++u) {
+        float a = acc[u];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if ((threadIdx.x & 31) == 0) red[u][threadIdx.x >> 5] = a;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < nt) {
         float s = 0.f;
-        for (int k = 0; k < kSeThreads / 32; ++k) s += red[k];
-        partial[static_cast<long long>(t) * nchunks + chunk] = s;
+        for (int k = 0; k < kSeThreads / 32; ++k) s += red[threadIdx.x][k];
+        partial[static_cast<long long>(t0 + threadIdx.x) * nchunks + chunk] = s;
     }
 }
 
@@ -124,11 +175,27 @@ namespace morph {
 
 struct BwdPlan {
     BwdTap* d_taps = nullptr;
-    int ntaps = 0;
+    BwdRow* d_rows = nullptr;
+    int ntaps = 0, nrows = 0;
     ~BwdPlan() {
         if (d_taps) cudaFree(d_taps);
+        if (d_rows) cudaFree(d_rows);
     }
 };
+
+typedef void (*BwdInputKernel)(BwdImage, const int32_t*, const float*, const BwdTap*, const BwdRow*, int, float*);
+typedef void (*BwdSeKernel)(BwdImage, const int32_t*, const float*, const BwdTap*, int, SeChunks, int, float*);
+
+template <int SGN>
+static BwdInputKernel input_kernel(int dt) {
+    return dt == MORPH_U8 ? k_bwd_input<SGN, MORPH_U8> : dt == MORPH_U16 ? k_bwd_input<SGN, MORPH_U16>
+                                                                          : k_bwd_input<SGN, MORPH_I32>;
+}
+template <int SGN>
+static BwdSeKernel se_kernel(int dt) {
+    return dt == MORPH_U8 ? k_bwd_se_partial<SGN, MORPH_U8> : dt == MORPH_U16 ? k_bwd_se_partial<SGN, MORPH_U16>
+                                                                               : k_bwd_se_partial<SGN, MORPH_I32>;
+}
 
 }  // namespace morph
 
@@ -162,37 +229,69 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
         if (taps.size() > 65535) return MORPH_E_UNSUPPORTED;   // one grid row of partial sums per tap
         plan = std::make_shared<BwdPlan>();
         plan->ntaps = static_cast<int>(taps.size());
+        std::vector<BwdRow> trows;            // taps are in box order, so each SE row's taps are contiguous
+        for (int t = 0; t < plan->ntaps; ++t) {
+            if (trows.empty() || trows.back().dy != taps[t].dy) trows.push_back(BwdRow{taps[t].dy, t, t});
+            trows.back().t1 = t + 1;
+        }
+        plan->nrows = static_cast<int>(trows.size());
         if (plan->ntaps > 0) {
             MORPH_CUDA_TRY(cudaMalloc(&plan->d_taps, taps.size() * sizeof(BwdTap)));
             MORPH_CUDA_TRY(cudaMemcpy(plan->d_taps, taps.data(), taps.size() * sizeof(BwdTap),
+                                      cudaMemcpyHostToDevice));
+            MORPH_CUDA_TRY(cudaMalloc(&plan->d_rows, trows.size() * sizeof(BwdRow)));
+            MORPH_CUDA_TRY(cudaMemcpy(plan->d_rows, trows.data(), trows.size() * sizeof(BwdRow),
                                       cudaMemcpyHostToDevice));
         }
         ctx->aux_plans.emplace(key, plan);
     }
     BwdImage im{f->data, f->dtype, f->n, f->h, f->w, f->row_stride, f->batch_stride, sgn};
     const long long total = static_cast<long long>(f->n) * f->h * f->w;
+    // chunks of the SE-gradient sums: RB rows x CB columns of one image
+    SeChunks ch;
+    ch.CB = std::min(f->w, kSeChunk);
+    ch.RB = std::max(1, kSeChunk / ch.CB);
+    ch.cx = (f->w + ch.CB - 1) / ch.CB;
+    ch.cy = (f->h + ch.RB - 1) / ch.RB;
+    ch.cbm = ch.CB == 1 ? 0u : static_cast<uint32_t>(((uint64_t(1) << 32) + ch.CB - 1) / ch.CB);
+    const long long nchunks_ll = static_cast<long long>(f->n) * ch.cy * ch.cx;
+    if (nchunks_ll > (1LL << 30)) return MORPH_E_UNSUPPORTED;
+    const int nchunks = static_cast<int>(nchunks_ll);
+    // workspace: q (one float per pixel), then the partial sums
+    const size_t q_bytes = (static_cast<size_t>(total) * sizeof(float) + 255) & ~size_t(255);
+    const size_t part_bytes = grad_se ? static_cast<size_t>(plan->ntaps) * nchunks * sizeof(float) : 0;
+    void* ws = nullptr;
+    int rc = ctx_workspace(ctx, q_bytes + part_bytes, &ws);
+    if (rc) return rc;
+    float* q = static_cast<float*>(ws);
+    if (plan->ntaps > 0) {
+        const unsigned blocks = static_cast<unsigned>(std::min<long long>((total + 255) / 256, ctx->num_sms * 16LL));
+        prof_begin(ctx, st, "k_bwd_share");
+        k_bwd_share<<<blocks, 256, 0, st>>>(grad_out, cD, q, total);
+        prof_end(ctx, st);
+        ctx->launches += 1;
+        MORPH_CUDA_TRY(cudaGetLastError());
+    }
     if (grad_in) {
-        long long blocks = (total + 255) / 256;
-        if (blocks > ctx->num_sms * 16LL) blocks = ctx->num_sms * 16LL;
+        const int bx = std::min(256, ((f->w + 31) / 32) * 32);
+        const long long rows = static_cast<long long>(f->n) * f->h;
+        dim3 grid(static_cast<unsigned>((f->w + bx - 1) / bx), static_cast<unsigned>(std::min<long long>(rows, 65535)));
         prof_begin(ctx, st, "k_bwd_input");
-        k_bwd_input<<<static_cast<unsigned>(blocks), 256, 0, st>>>(im, D, cD, grad_out, plan->d_taps, plan->ntaps,
-                                                                  grad_in);
+        const BwdInputKernel kin = sgn > 0 ? input_kernel<1>(f->dtype) : input_kernel<-1>(f->dtype);
+        kin<<<grid, bx, 0, st>>>(im, D, q, plan->d_taps, plan->d_rows, plan->nrows, grad_in);
         prof_end(ctx, st);
         ctx->launches += 1;
         MORPH_CUDA_TRY(cudaGetLastError());
     }
     if (grad_se) {
         const int nbox = b->kh * b->kw;
-        const int nchunks = static_cast<int>((total + kSeChunk - 1) / kSeChunk);
         float* partial = nullptr;
         if (plan->ntaps > 0) {
-            void* ws = nullptr;
-            int rc = ctx_workspace(ctx, static_cast<size_t>(plan->ntaps) * nchunks * sizeof(float), &ws);
-            if (rc) return rc;
-            partial = static_cast<float*>(ws);
-            dim3 grid(nchunks, plan->ntaps);
+            partial = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + q_bytes);
+            dim3 grid(nchunks, (plan->ntaps + kSeTaps - 1) / kSeTaps);
             prof_begin(ctx, st, "k_bwd_se_partial");
-            k_bwd_se_partial<<<grid, kSeThreads, 0, st>>>(im, D, cD, grad_out, plan->d_taps, nchunks, partial);
+            const BwdSeKernel kse = sgn > 0 ? se_kernel<1>(f->dtype) : se_kernel<-1>(f->dtype);
+            kse<<<grid, kSeThreads, 0, st>>>(im, D, q, plan->d_taps, plan->ntaps, ch, nchunks, partial);
             prof_end(ctx, st);
             ctx->launches += 1;
             MORPH_CUDA_TRY(cudaGetLastError());

@@ -110,3 +110,15 @@ def test_erosion_backward_irregular_se_with_ties():
     se = wl.se_random(g, 5, 7, 0.6, 2, origin=(3, 1))
     up = g.standard_normal(x.shape).astype(np.float32)
     _check_erode(x, se.offset.astype(np.float32), se.mask, se.origin, 4, up)
+
+
+@pytest.mark.parametrize("shape", [(2, 1, 5, 9000), (1, 1, 300, 1), (3, 1, 70, 33), (1, 1, 1, 40)])
+def test_chunking_edge_shapes(shape):
+    # SE-gradient chunks are rows x columns of one image: rows wider than a chunk,
+    # one-column images, ragged chunk tails
+    g = wl.rng(sum(shape))
+    x = g.integers(0, 8, size=shape).astype(np.float32)
+    se = wl.se_random(g, 3, 5, 0.7, 3, origin=(1, 2))
+    up = g.standard_normal(shape).astype(np.float32)
+    _check(x, se.offset.astype(np.float32), se.mask, se.origin, 8, up)
+    _check_erode(x, se.offset.astype(np.float32), se.mask, se.origin, 8, up)
