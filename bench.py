@@ -46,7 +46,11 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FFT-form comparison")
-    ap.add_argument("--cpu-rows", type=int, default=48, help="oracle sample: rows per operation")
+    ap.add_argument("--cpu-rows", type=int, default=0,
+                    help="cpu_baseline: image rows per operation on all cores (0 = all rows)")
+    ap.add_argument("--cpu-rows-single", type=int, default=96,
+                    help="cpu_baseline: image rows per operation single-threaded")
+    ap.add_argument("--ref-rows", type=int, default=128, help="--impl reference: image rows per operation per step")
     ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "x1", "x2", "one"], default="c2",
                     help="c2 (default) is the headline workload; the others time the remaining configurations; "
                          "'one' times a single dilation of the sweeps' recipe (--image, --levels, --filter, --method)")
@@ -54,6 +58,10 @@ def _args():
     ap.add_argument("--levels", type=int, default=256, help="one: grey levels L (image and offsets in 0..L-1)")
     ap.add_argument("--filter", type=int, default=64, help="one: full-support filter side")
     ap.add_argument("--method", default="auto", help="one: auto | direct_fp8 | fft_f32 | fft_f64 | ntt")
+    ap.add_argument("--se", default="full", choices=["full", "convex", "disk"],
+                    help="one: full-support square, convex-hull support (as C3) or flat disk")
+    ap.add_argument("--max-off", type=int, default=-1, help="one: largest SE offset (default L - 1)")
+    ap.add_argument("--smooth", action="store_true", help="one: Gaussian-blurred image (as C3) instead of uniform")
     return ap.parse_args()
 
 
@@ -176,8 +184,8 @@ def run_reference(args, ws, rank):
     from paper_2305_03018_gb300 import workloads as wl
     oracle.build()
     probs = wl.c2_large_filter()
-    rows = max(1, args.cpu_rows // 3)
     H = probs[0].f.shape[1]
+    rows = max(1, min(args.ref_rows, H - 1))
     cores = oracle.max_threads()
 
     def step(k):
@@ -400,12 +408,15 @@ def _time_forms(ctx, probs, f_dev, L, ref_outs, px_per_step, stream, steps):
 
 
 def _cpu_baseline(args, probs, outs):
+    """The oracle on the host cores: all rows of the step's 4 operations with
+    every thread (each output compared with the GPU's, bit for bit), and a
+    row sample single-threaded."""
     import numpy as np
 
     import oracle
     oracle.build()
-    rows = args.cpu_rows
     H, W = probs[0].f.shape[1:]
+    rows = H if args.cpu_rows <= 0 else min(H, args.cpu_rows)
     r0 = (H - rows) // 2
     cores = oracle.max_threads()
     t0 = time.perf_counter()
@@ -416,9 +427,20 @@ def _cpu_baseline(args, probs, outs):
         got = o[:, r0:r0 + rows].cpu().numpy()
         exact &= bool(np.array_equal(got, ref[:, r0:r0 + rows]))
     dt = time.perf_counter() - t0
+    srows = min(H, max(1, args.cpu_rows_single))
+    s0 = (H - srows) // 2
+    t1 = time.perf_counter()
+    for p in probs:
+        fn = oracle.dilate if p.op == "dilate" else oracle.erode
+        fn(p.f, p.L, p.se.mask, p.se.offset, p.se.origin, rows=(s0, s0 + srows), nthreads=1)
+    dt1 = time.perf_counter() - t1
+    whole = "all rows" if rows == H else f"rows {r0}..{r0 + rows - 1}"
     return {"value": 4 * rows * W / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"rows {r0}..{r0 + rows - 1} of each of the 4 operations ({4 * rows * W} px)",
-            "parity_on_sample": "bit-exact" if exact else "MISMATCH"}
+            "sample": f"{whole} of each of the 4 operations ({4 * rows * W} px, {dt:.1f} s on {cores} threads)",
+            "parity_on_sample": "bit-exact" if exact else "MISMATCH",
+            "single_thread": {"value": 4 * srows * W / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": f"rows {s0}..{s0 + srows - 1} of each of the 4 operations "
+                                        f"({4 * srows * W} px, {dt1:.1f} s)"}}
 
 
 # ------------------------------------------------------- other configurations
@@ -612,8 +634,10 @@ def run_sweep(args, ws, rank, local):
 
 def run_one(args, ws, rank, local):
     """One dilation of an n x n randint image by a k x k full-support randint
-    filter (the recipe of the paper's runtime experiments, Sec. 4.1) with one
-    method: warm-up, then `steps` timed calls, each with its kernel times."""
+    filter (the recipe of the paper's runtime experiments, Sec. 4.1), or of
+    the C3 recipe's smooth image / convex SE, with one method: warm-up, then
+    `steps` timed calls, each with its kernel times."""
+    import numpy as np
     import torch
 
     from paper_2305_03018_gb300 import workloads as wl
@@ -621,9 +645,20 @@ def run_one(args, ws, rank, local):
     torch.cuda.set_device(local)
     ctx = get_context(local)
     n, L, k = args.image, args.levels, args.filter
+    mo = L - 1 if args.max_off < 0 else args.max_off
     g = wl.rng(1000 * n + k + (4 if L <= 16 else 8))
-    f = torch.from_numpy(wl.uniform_image(g, (1, n, n), L)).cuda()
-    se = wl.se_full_random(g, k, L - 1)
+    if args.smooth:
+        img = wl.gauss_blurred_u8(g, n, 8.0)[None]
+        img = (img.astype(np.int32) * L // 256).astype(np.uint8)
+    else:
+        img = wl.uniform_image(g, (1, n, n), L)
+    f = torch.from_numpy(img).cuda()
+    if args.se == "convex":
+        se = wl.se_random_convex(g, k, 12, mo)
+    elif args.se == "disk":
+        se = wl.se_flat_disk(k // 2)
+    else:
+        se = wl.se_full_random(g, k, mo)
     info = ctx.plan(f, L, se, method=args.method)
     out = torch.empty((1, n, n), dtype=torch.int32, device="cuda")
     for _ in range(max(1, args.warmup)):
@@ -641,11 +676,19 @@ def run_one(args, ws, rank, local):
     ctx.check()
     ms = e0.elapsed_time(e1) / max(1, args.steps)
     line = {"metric": METRIC, "workload": "one", "unit": "ms per dilation", "value": ms, "steps": args.steps,
-            "config": {"image": n, "L": L, "filter": k, "method": args.method,
+            "config": {"image": n, "L": L, "filter": k, "se": args.se, "max_off": mo, "smooth": args.smooth,
+                       "taps": int(np.count_nonzero(se.mask)), "method": args.method,
                        "method_used": {1: "direct_fp8", 2: "fft_f32", 3: "fft_f64", 4: "ntt"}.get(info.method),
                        "fft_nx": info.fft_nx, "fft_ny": info.fft_ny, "tile": [info.tile_h, info.tile_w],
                        "workspace_bytes": info.workspace_bytes, "est_ops": info.est_flop},
             "kernel_ms_per_call": {kk: v[1] / max(1, args.steps) for kk, v in kt.items()}}
+    if info.method == 1 and "k_direct_fp8" in kt:
+        mp, src = _peaks()
+        peak = 2.0 * float(mp.get("bf16_tflops_sustained", mp.get("bf16_tflops")))
+        achieved = info.est_flop / (kt["k_direct_fp8"][1] / max(1, args.steps) * 1e-3) / 1e12
+        line["roofline"] = {"kernel": "k_direct_fp8", "bound": "tensor", "achieved": achieved, "peak": peak,
+                            "unit": "TFLOP/s", "frac": achieved / peak,
+                            "peak_source": f"{src} bf16 sustained x 2 (nominal fp8/bf16 dense ratio)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

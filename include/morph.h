@@ -131,6 +131,16 @@ int morph_ctx_destroy(morph_ctx *ctx);
 int morph_plan_query(morph_ctx *ctx, const morph_image *f, const morph_se *b, int op,
                      const morph_opts *opts, morph_plan_info *out);
 
+/* Device workspace (bytes) that a call will grow the context's workspace to:
+ * op 0 = morph_dilate, 1 = morph_erode, 2 = morph_dilate_backward, 3 =
+ * morph_erode_backward, for `f` and `b` under `opts` (nullable = AUTO).
+ * Host-only: no device work, no allocation; `ctx` may be NULL (then the AUTO
+ * decision is not cached).  The workspace is owned by the context and reused
+ * by later calls; composite and 3-D calls additionally use a second
+ * workspace of 2 resp. 3 int32 images. */
+int morph_workspace_size(morph_ctx *ctx, const morph_image *f, const morph_se *b, int op,
+                         const morph_opts *opts, size_t *bytes);
+
 /* Dilation, Eq. 6 (Steps 1-3 of Sec. 3).  out: int32 [n][h][w] device;
  * out_count: nullable int32 [n][h][w] device, the top coefficient.
  * The first call for a new (SE, L, shape, method) builds and caches a plan,

@@ -14,6 +14,8 @@
 // with the tap direction and the sign of b reversed (sgn = -1):
 //   grad_in(p)  = sum_{y, p - y in F, f(p) - b(y) = E(p - y)} g(p - y) / cE(p - y)
 //   grad_se(y)  = - sum_{x, x + y in F, f(x + y) - b(y) = E(x)} g(x) / cE(x)
+#include <algorithm>
+
 #include "morph_internal.h"
 #include "ptx.cuh"
 
@@ -199,6 +201,29 @@ static BwdSeKernel se_kernel(int dt) {
 
 }  // namespace morph
 
+static SeChunks se_chunks(const morph_image* f) {
+    SeChunks ch;
+    ch.CB = std::min(f->w, kSeChunk);
+    ch.RB = std::max(1, kSeChunk / ch.CB);
+    ch.cx = (f->w + ch.CB - 1) / ch.CB;
+    ch.cy = (f->h + ch.RB - 1) / ch.RB;
+    ch.cbm = ch.CB == 1 ? 0u : static_cast<uint32_t>(((uint64_t(1) << 32) + ch.CB - 1) / ch.CB);
+    return ch;
+}
+
+static size_t share_bytes(const morph_image* f) {
+    const size_t total = static_cast<size_t>(f->n) * f->h * f->w;
+    return (total * sizeof(float) + 255) & ~size_t(255);
+}
+
+size_t morph::backward_workspace_bytes(const morph_image* f, const morph_se* b) {
+    int ntaps = 0;
+    for (int t = 0; t < b->kh * b->kw; ++t) ntaps += b->mask[t] ? 1 : 0;
+    const SeChunks ch = se_chunks(f);
+    const size_t nchunks = static_cast<size_t>(f->n) * ch.cy * ch.cx;
+    return share_bytes(f) + static_cast<size_t>(ntaps) * nchunks * sizeof(float);
+}
+
 static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b, const int32_t* D,
                          const int32_t* cD, const float* grad_out, float* grad_in, float* grad_se,
                          morph_stream_t stream, int sgn) {
@@ -248,17 +273,12 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
     BwdImage im{f->data, f->dtype, f->n, f->h, f->w, f->row_stride, f->batch_stride, sgn};
     const long long total = static_cast<long long>(f->n) * f->h * f->w;
     // chunks of the SE-gradient sums: RB rows x CB columns of one image
-    SeChunks ch;
-    ch.CB = std::min(f->w, kSeChunk);
-    ch.RB = std::max(1, kSeChunk / ch.CB);
-    ch.cx = (f->w + ch.CB - 1) / ch.CB;
-    ch.cy = (f->h + ch.RB - 1) / ch.RB;
-    ch.cbm = ch.CB == 1 ? 0u : static_cast<uint32_t>(((uint64_t(1) << 32) + ch.CB - 1) / ch.CB);
+    const SeChunks ch = se_chunks(f);
     const long long nchunks_ll = static_cast<long long>(f->n) * ch.cy * ch.cx;
     if (nchunks_ll > (1LL << 30)) return MORPH_E_UNSUPPORTED;
     const int nchunks = static_cast<int>(nchunks_ll);
     // workspace: q (one float per pixel), then the partial sums
-    const size_t q_bytes = (static_cast<size_t>(total) * sizeof(float) + 255) & ~size_t(255);
+    const size_t q_bytes = share_bytes(f);
     const size_t part_bytes = grad_se ? static_cast<size_t>(plan->ntaps) * nchunks * sizeof(float) : 0;
     void* ws = nullptr;
     int rc = ctx_workspace(ctx, q_bytes + part_bytes, &ws);

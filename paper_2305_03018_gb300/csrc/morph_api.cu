@@ -248,8 +248,10 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
     if (method == MORPH_NTT) { *route = ROUTE_NTT; return MORPH_OK; }
     if (method != MORPH_AUTO) return MORPH_E_INVAL;
     const std::string key = "auto|" + plan_key(f, se, erode, 0);
-    auto it = ctx->route_cache.find(key);
-    if (it != ctx->route_cache.end()) { *route = it->second; return MORPH_OK; }
+    if (ctx) {
+        auto it = ctx->route_cache.find(key);
+        if (it != ctx->route_cache.end()) { *route = it->second; return MORPH_OK; }
+    }
     DirectPlan dp;
     int rc = plan_direct_host(f, se, erode, &dp);
     if (rc) return rc;
@@ -275,7 +277,7 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
         }
     }
     (void)unproven;
-    ctx->route_cache.emplace(key, *route);
+    if (ctx) ctx->route_cache.emplace(key, *route);
     return MORPH_OK;
 }
 
@@ -468,6 +470,43 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         out->tile_h = q.To_y;
         out->est_flop = q.flop;
         out->workspace_bytes = q.ws_bytes;
+    }
+    return MORPH_OK;
+}
+
+int morph_workspace_size(morph_ctx* ctx, const morph_image* f, const morph_se* b, int op, const morph_opts* opts,
+                         size_t* bytes) {
+    if (!bytes || op < 0 || op > 3) return MORPH_E_INVAL;
+    int rc = validate(f, b);
+    if (rc) return rc;
+    *bytes = 0;
+    if (op >= 2) {
+        *bytes = backward_workspace_bytes(f, b);
+        return MORPH_OK;
+    }
+    const int erode = op;
+    const int method = opts ? opts->method : MORPH_AUTO;
+    const bool unproven = opts && (opts->flags & MORPH_F_ALLOW_UNPROVEN_F32);
+    EffSE e;
+    effective_se(b, erode, &e);
+    int taps = 0;
+    for (int t = 0; t < b->kh * b->kw; ++t) taps += b->mask[t] ? 1 : 0;
+    if (taps == 0) return MORPH_OK;
+    int route = ROUTE_DIRECT;
+    rc = choose_route(ctx, f, &e.se, erode, method, unproven, &route);
+    if (rc) return rc;
+    if (route == ROUTE_DIRECT) {
+        *bytes = planes_bytes(f);
+    } else if (route == ROUTE_NTT) {
+        NttPlan q;
+        rc = plan_ntt_tiles(f, &e.se, &q);
+        if (rc) return rc;
+        *bytes = q.ws_bytes;
+    } else {
+        FftPlan q;
+        rc = plan_fft_tiles(f, &e.se, route == ROUTE_FFT32 ? 4 : 8, unproven, &q);
+        if (rc) return rc;
+        *bytes = q.ws_bytes;
     }
     return MORPH_OK;
 }

@@ -226,6 +226,8 @@ int launch_ntt(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int erode
                cudaStream_t st);
 int launch_ntt_in(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
                   void* buf, cudaStream_t st);
+// device workspace of morph_dilate_backward / morph_erode_backward (shares + partial sums)
+size_t backward_workspace_bytes(const morph_image* f, const morph_se* b);
 double fft_error_bound(const FftAxis& ax, const FftAxis& ay, const FftAxis& ar, double sqrtP, int taps, double u);
 
 }  // namespace morph

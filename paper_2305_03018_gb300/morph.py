@@ -103,6 +103,8 @@ _SIGS = {
                                            ctypes.POINTER(morph_opts), ctypes.POINTER(ctypes.c_void_p)]),
     "morph_batch_launch": (ctypes.c_int, [_P, _P]),
     "morph_batch_destroy": (ctypes.c_int, [_P]),
+    "morph_workspace_size": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), ctypes.c_int,
+                                            ctypes.POINTER(morph_opts), ctypes.POINTER(ctypes.c_size_t)]),
     "morph_stream_check": (ctypes.c_int, [_P, _P]),
     "morph_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "morph_launch_count": (ctypes.c_uint64, [_P]),
@@ -209,6 +211,15 @@ def morph_dilate_backward(ctx, image, se, d_ptr, cd_ptr, g_ptr, gin_ptr, gse_ptr
 def morph_erode_backward(ctx, image, se, e_ptr, ce_ptr, g_ptr, gin_ptr, gse_ptr, stream) -> int:
     return load_library().morph_erode_backward(ctx, ctypes.byref(image), ctypes.byref(se), e_ptr, ce_ptr, g_ptr,
                                                gin_ptr, gse_ptr, stream)
+
+
+def morph_workspace_size(ctx, image, se, op, opts) -> int:
+    """Device workspace (bytes) a call would use; op 0/1 dilate/erode, 2/3 their backward."""
+    out = ctypes.c_size_t(0)
+    check(load_library().morph_workspace_size(ctx, ctypes.byref(image), ctypes.byref(se), int(op),
+                                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(out)),
+          "morph_workspace_size")
+    return int(out.value)
 
 
 def morph_run_batch(ctx, problems, opts, stream) -> int:
@@ -444,6 +455,11 @@ class Context:
         st = stream if stream is not None else current_stream_handle(f.device)
         check(fn(self.handle, img, sv.c, out.data_ptr(), make_opts(method), st), "morph_" + which)
         return out
+
+    def workspace_size(self, f, L, se, op=0, method="auto", allow_unproven_f32=False):
+        """Bytes of device workspace: op 0/1 dilation/erosion, 2/3 their backward."""
+        sv = se_view(se)                         # keeps the SE arrays alive during the call
+        return morph_workspace_size(self.handle, make_image(f, L), sv.c, op, make_opts(method, allow_unproven_f32))
 
     def plan(self, f, L, se, op=0, method="auto", allow_unproven_f32=False, **_):
         img = make_image(f, L)

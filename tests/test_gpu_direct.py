@@ -161,3 +161,21 @@ def test_data_error_reported(ctx):
         ctx.check()
     assert ei.value.status == MORPH_E_RANGE
     ctx.check()                                  # the error word was cleared
+
+
+def test_workspace_size_matches_plan_and_is_host_only():
+    from paper_2305_03018_gb300.morph import get_context
+    ctx = get_context(0)
+    g = wl.rng(61)
+    f = torch.from_numpy(g.integers(0, 64, size=(2, 200, 300)).astype(np.uint8)).cuda()
+    se = wl.se_random(g, 9, 7, 0.6, 5)
+    for method in ("direct_fp8", "fft_f64", "ntt", "auto"):
+        for op in (0, 1):
+            ws = ctx.workspace_size(f, 64, se, op=op, method=method)
+            assert ws == ctx.plan(f, 64, se, op=op, method=method).workspace_bytes, (method, op)
+    assert ctx.workspace_size(f, 64, se, op=0, method="direct_fp8") == 2 * 200 * 64 * 304
+    # backward: one float share per pixel (rounded to 256 B) plus one partial sum per (tap, chunk)
+    ntaps = int(np.count_nonzero(se.mask))
+    chunks = 2 * ((200 + (8192 // 300) - 1) // (8192 // 300))
+    exp = ((2 * 200 * 300 * 4 + 255) // 256) * 256 + ntaps * chunks * 4
+    assert ctx.workspace_size(f, 64, se, op=2) == exp == ctx.workspace_size(f, 64, se, op=3)

@@ -1,0 +1,84 @@
+"""Host-side planning through the C ABI, without a GPU: morph_workspace_size
+with a NULL context runs the validation, the route choice (AUTO's fitted
+time models), the FP8, FFT and NTT tilings and the backward chunking on the
+host only.  Image data pointers are never dereferenced on this path."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2305_03018_gb300 import morph as M
+from paper_2305_03018_gb300 import workloads as wl
+
+pytestmark = pytest.mark.timeout(60)
+_DUMMY = ctypes.create_string_buffer(16)
+
+
+def _img(n, h, w, L, dtype=M.MORPH_U8):
+    im = M.morph_image()
+    im.data = ctypes.addressof(_DUMMY)
+    im.dtype = dtype
+    im.n, im.h, im.w = n, h, w
+    im.row_stride = w
+    im.batch_stride = h * w
+    im.L = L
+    return im
+
+
+def _ws(im, se, op, method="auto"):
+    sv = M.se_view(se)
+    return M.morph_workspace_size(None, im, sv.c, op, M.make_opts(method))
+
+
+def test_direct_and_backward_sizes_follow_their_layouts():
+    g = wl.rng(61)
+    se = wl.se_random(g, 9, 7, 0.6, 5)
+    im = _img(2, 200, 300, 64)
+    # indicator planes: n h L round16(w) bytes
+    assert _ws(im, se, 0, "direct_fp8") == _ws(im, se, 1, "direct_fp8") == 2 * 200 * 64 * 304
+    # backward: a float share per pixel (256-byte rounded) + a partial sum per (tap, chunk of <= 8192 px)
+    ntaps = int(np.count_nonzero(se.mask))
+    rows_per_chunk = 8192 // 300
+    chunks = 2 * -(-200 // rows_per_chunk)
+    exp = -(-2 * 200 * 300 * 4 // 256) * 256 + ntaps * chunks * 4
+    assert _ws(im, se, 2) == _ws(im, se, 3) == exp
+
+
+def test_transform_routes_plan_on_the_host():
+    g = wl.rng(62)
+    for (n, L, k, mo) in [(512, 256, 64, 255), (2048, 16, 204, 15), (300, 64, 31, 4), (64, 2, 3, 0)]:
+        se = wl.se_full_random(g, k, mo)
+        im = _img(1, n, n, L)
+        ntt = _ws(im, se, 0, "ntt")
+        f64 = _ws(im, se, 0, "fft_f64")
+        assert ntt > 0 and f64 > 0
+        sizes = {ntt, f64, _ws(im, se, 0, "direct_fp8")}
+        try:
+            sizes.add(_ws(im, se, 0, "fft_f32"))
+        except M.MorphError as e:                  # FP32 refused where its bound fails
+            assert e.status == M.MORPH_E_PRECISION
+        assert _ws(im, se, 0, "auto") in sizes
+
+
+def test_auto_prefers_ntt_for_8bit_offsets_and_fp8_for_small_flat():
+    g = wl.rng(63)
+    big = wl.se_full_random(g, 96, 255)
+    im = _img(1, 512, 512, 256)
+    assert _ws(im, big, 0, "auto") == _ws(im, big, 0, "ntt")
+    small = wl.se_flat_square(3)
+    im2 = _img(1, 1024, 1024, 16)
+    assert _ws(im2, small, 0, "auto") == _ws(im2, small, 0, "direct_fp8")
+
+
+def test_invalid_requests_are_refused():
+    se = wl.se_flat_square(3)
+    sv = M.se_view(se)
+    bytes_ = ctypes.c_size_t(0)
+    lib = M.load_library()
+    im = _img(1, 10, 10, 16)
+    assert lib.morph_workspace_size(None, ctypes.byref(im), ctypes.byref(sv.c), 4, None, ctypes.byref(bytes_)) \
+        == M.MORPH_E_INVAL
+    bad = _img(1, 10, 10, 1)                       # L < 2
+    assert lib.morph_workspace_size(None, ctypes.byref(bad), ctypes.byref(sv.c), 0, None, ctypes.byref(bytes_)) \
+        == M.MORPH_E_INVAL
+    assert lib.morph_workspace_size(None, ctypes.byref(im), ctypes.byref(sv.c), 0, None, None) == M.MORPH_E_INVAL
