@@ -219,6 +219,7 @@ def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
 
+    from paper_2305_03018_gb300 import morph as M
     from paper_2305_03018_gb300 import workloads as wl
     from paper_2305_03018_gb300.morph import get_context
 
@@ -281,12 +282,56 @@ def run_ours(args, ws, rank, local):
     ms = max_over_ranks(ms, dist, dev)
     value = job_throughput(px_per_step, ws, ms)
 
-    # ---- end to end through the C ABI: pinned host -> device -> ops -> host
+    # ---- end to end through the C ABI: pinned host -> device -> ops -> host,
+    # every step's copies inside the timed region, pipelined: the input upload
+    # and each result's download run on their own streams while the next
+    # operation computes (inputs and outputs double-buffered, event-ordered)
     h2d = f_host.numel() * f_host.element_size()
     d2h = sum(o.numel() * o.element_size() for o in outs_host)
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    f_bufs = [f_dev, torch.empty_like(f_dev)]
+    out_bufs = [outs, [torch.empty_like(o) for o in outs]]
+    host_bufs = [outs_host, [torch.empty_like(o).pin_memory() for o in outs_host]]
+    f_free = [torch.cuda.Event(), torch.cuda.Event()]
+    out_free = [[torch.cuda.Event() for _ in probs] for _ in range(2)]
+    for ev in f_free + out_free[0] + out_free[1]:
+        ev.record(stream)
+    cs = M.current_stream_handle(dev)
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s_in.wait_event(e0)
+    s_out.wait_event(e0)
+    for k in range(args.steps):
+        b = k % 2
+        s_in.wait_event(f_free[b])
+        with torch.cuda.stream(s_in):
+            f_bufs[b].copy_(f_host, non_blocking=True)
+        ready = torch.cuda.Event()
+        ready.record(s_in)
+        stream.wait_event(ready)
+        for i, p in enumerate(probs):
+            stream.wait_event(out_free[b][i])
+            (ctx.dilate if p.op == "dilate" else ctx.erode)(f_bufs[b], L, p.se, method="direct_fp8",
+                                                            out=out_bufs[b][i], stream=cs)
+            done = torch.cuda.Event()
+            done.record(stream)
+            s_out.wait_event(done)
+            with torch.cuda.stream(s_out):
+                host_bufs[b][i].copy_(out_bufs[b][i], non_blocking=True)
+            out_free[b][i].record(s_out)
+        f_free[b].record(stream)
+    stream.wait_stream(s_in)
+    stream.wait_stream(s_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ctx.check()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    assert all(torch.equal(host_bufs[(args.steps - 1) % 2][i], outs[i].cpu()) for i in range(len(probs)))
+    # the same with every copy serialised on the compute stream (no overlap), for reference
+    torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
         f_dev.copy_(f_host, non_blocking=True)
@@ -295,8 +340,7 @@ def run_ours(args, ws, rank, local):
             oh.copy_(o, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    serial_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     e2e = job_throughput(px_per_step, ws, e2e_ms)
 
@@ -335,7 +379,9 @@ def run_ours(args, ws, rank, local):
             "roofline": roof, "clocks": clocks, "gpu_launches": launches,
             "forms": forms,
             "vs_fp64_form": (value / ws / forms["fft_f64"]["value"]) if forms.get("fft_f64", {}).get("value") else None,
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "copies": "pinned host buffers; upload and downloads on their own streams, double-buffered",
+                    "serial_value": job_throughput(px_per_step, ws, serial_ms)}}
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 only
     if ws == 1 and not args.no_cpu_baseline:
