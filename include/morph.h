@@ -59,7 +59,7 @@ enum morph_status {
     MORPH_E_PRECISION = 4,   /* FP32 FFT requested but its round-off bound fails */
     MORPH_E_CUDA = 5,        /* a CUDA runtime/driver call failed */
     MORPH_E_TIMEOUT = 6,     /* a bounded device-side wait gave up */
-    MORPH_E_UNSUPPORTED = 7  /* valid request outside what this build implements */
+    MORPH_E_UNSUPPORTED = 7  /* valid request outside what the library implements */
 };
 
 /* ------------------------------------------------------------- inputs */
