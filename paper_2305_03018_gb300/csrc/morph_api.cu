@@ -386,6 +386,9 @@ int morph_ctx_destroy(morph_ctx* ctx) {
         cudaEventDestroy(r.b);
     }
     for (auto e : ctx->prof_pool) cudaEventDestroy(e);
+    for (auto s : ctx->branch) cudaStreamDestroy(s);
+    for (auto e : ctx->branch_ev) cudaEventDestroy(e);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->ws2) cudaFree(ctx->ws2);
     if (ctx->d_err) cudaFree(ctx->d_err);

@@ -5,7 +5,11 @@
 //   one persistent k_direct_fp8 launch over the concatenated tile list, with
 //     the problems' tensor maps in device memory (tiles of the most expensive
 //     problems first, so the cheap ones fill the tail),
-// and the FFT problems follow with their own launch sequences.  The same
+// and the transform-route problems (FFT, NTT) follow with their own launch
+// sequences, spread over up to four branch streams (heaviest first onto the
+// least-loaded branch, each with its own workspace slice) that fork from and
+// join back into the caller's stream, so small problems run side by side.
+// The same
 // enqueue serves morph_run_batch (direct launches into the context's batch
 // workspace) and morph_batch_capture (launches recorded once into a CUDA
 // graph that owns its workspace).
@@ -32,6 +36,9 @@ struct morph_batch {
     std::vector<int> direct_order;       // items on the direct route, heaviest tiles first
     std::vector<int> fft_items;
     std::vector<int> empty_items;
+    int nbranch = 1;                          // branch streams for the transform-route problems
+    std::vector<std::vector<int>> branch_items;
+    size_t fft_stride = 0;                    // workspace slice per branch
     size_t jobs_off = 0, probs_off = 0, fft_off = 0, total_bytes = 0;
     long long enc_items = 0, total_tiles = 0;
     std::vector<EncodeJob> jobs;
@@ -53,6 +60,30 @@ struct morph_batch {
 namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+constexpr int kBatchBranches = 4;
+
+// The context's branch streams and events (created once, kept until the context is destroyed).
+int ensure_branches(morph_ctx* ctx, int n) {
+    if (!ctx->fork_ev) MORPH_CUDA_TRY(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+    while (static_cast<int>(ctx->branch.size()) < n) {
+        cudaStream_t s = nullptr;
+        MORPH_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        ctx->branch.push_back(s);
+        cudaEvent_t e = nullptr;
+        MORPH_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->branch_ev.push_back(e);
+    }
+    return MORPH_OK;
+}
+
+int launch_transform_item(morph_batch* b, int i, uint8_t* ws, cudaStream_t st) {
+    const auto& it = b->items[i];
+    return it.plan->route == ROUTE_NTT
+               ? launch_ntt_in(b->ctx, it.plan->ntt, &it.f, it.erode, it.out, it.cnt, ws, st)
+               : launch_fft_in(b->ctx, it.plan->fft, &it.f, it.erode, it.out, it.cnt, b->count_err, b->validate, ws,
+                               st);
+}
 
 // Host planning of every problem and the layout of the batch workspace.
 int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts* opts, morph_batch* b) {
@@ -93,8 +124,28 @@ int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts*
         const Plan& pl = *b->items[i].plan;
         fft_need = std::max(fft_need, pl.route == ROUTE_NTT ? pl.ntt.ws_bytes : pl.fft.ws_bytes);
     }
+    // branches: up to 4, within 8 GB of transform workspace in total
+    int S = std::min<int>(kBatchBranches, static_cast<int>(b->fft_items.size()));
+    while (S > 1 && fft_need * static_cast<size_t>(S) > (size_t(8) << 30)) --S;
+    b->nbranch = std::max(S, 1);
+    b->branch_items.assign(b->nbranch, {});
+    std::vector<std::pair<double, int>> cost;
+    for (int i : b->fft_items) {
+        const Plan& pl = *b->items[i].plan;
+        const double c = pl.route == ROUTE_NTT ? ntt_time_estimate(pl.ntt)
+                                               : pl.fft.flop / (pl.fft.prec == 4 ? 2.16e12 : 6.9e11);
+        cost.push_back({c, i});
+    }
+    std::stable_sort(cost.begin(), cost.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<double> load(b->nbranch, 0.0);
+    for (const auto& c : cost) {
+        const int s = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+        b->branch_items[s].push_back(c.second);
+        load[s] += c.first;
+    }
+    b->fft_stride = align_up(fft_need, 256);
     b->fft_off = off;
-    off = align_up(off + fft_need, 256);
+    off = align_up(off + b->fft_stride * b->nbranch, 256);
     b->total_bytes = std::max<size_t>(off, 256);
     b->count_err = opts ? opts->count_err : nullptr;
     b->validate = (opts && (opts->flags & MORPH_F_VALIDATE)) ? 1 : 0;
@@ -166,15 +217,30 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
     }
     if (b->count_err && !b->fft_items.empty())
         MORPH_CUDA_TRY(cudaMemsetAsync(b->count_err, 0, sizeof(float), st));
-    for (int i : b->fft_items) {
-        const auto& it = b->items[i];
-        int rc = it.plan->route == ROUTE_NTT
-                     ? launch_ntt_in(ctx, it.plan->ntt, &it.f, it.erode, it.out, it.cnt, ws + b->fft_off, st)
-                     : launch_fft_in(ctx, it.plan->fft, &it.f, it.erode, it.out, it.cnt, b->count_err, b->validate,
-                                     ws + b->fft_off, st);
-        if (rc) return rc;
+    if (b->fft_items.empty()) return MORPH_OK;
+    if (b->nbranch == 1) {
+        for (int i : b->fft_items) {
+            int rc = launch_transform_item(b, i, ws + b->fft_off, st);
+            if (rc) return rc;
+        }
+        return MORPH_OK;
     }
-    return MORPH_OK;
+    int rc = ensure_branches(ctx, b->nbranch);
+    if (rc) return rc;
+    MORPH_CUDA_TRY(cudaEventRecord(ctx->fork_ev, st));
+    int first_err = MORPH_OK;
+    for (int s = 0; s < b->nbranch; ++s) {
+        cudaStream_t bs = ctx->branch[s];
+        MORPH_CUDA_TRY(cudaStreamWaitEvent(bs, ctx->fork_ev, 0));
+        for (int i : b->branch_items[s]) {
+            if (first_err) break;
+            first_err = launch_transform_item(b, i, ws + b->fft_off + s * b->fft_stride, bs);
+        }
+        // join even after an error, so a capture in progress stays well-formed
+        MORPH_CUDA_TRY(cudaEventRecord(ctx->branch_ev[s], bs));
+        MORPH_CUDA_TRY(cudaStreamWaitEvent(st, ctx->branch_ev[s], 0));
+    }
+    return first_err;
 }
 
 int upload_descriptors(morph_batch* b, uint8_t* ws, cudaStream_t st, bool sync_copy) {

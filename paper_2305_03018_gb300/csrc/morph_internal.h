@@ -174,6 +174,9 @@ struct morph_ctx {
     void* ws2 = nullptr;                  // intermediate images of composite operators
     size_t ws2_bytes = 0;
     uint64_t launches = 0;
+    std::vector<cudaStream_t> branch;     // batch branches for transform-route problems (created on demand)
+    std::vector<cudaEvent_t> branch_ev;   // their join events
+    cudaEvent_t fork_ev = nullptr;
     std::unordered_map<std::string, std::shared_ptr<morph::Plan>> plans;
     std::unordered_map<std::string, std::shared_ptr<void>> aux_plans;   // backward tap lists, ...
     std::unordered_map<std::string, int> route_cache;                   // AUTO decisions

@@ -91,3 +91,33 @@ def test_c5_full_batch_sampled(ctx):
         r0 = int(g.integers(0, H - 2))
         _check(p, o, c, rows=(r0, r0 + 2))
     b.close()
+
+
+@pytest.mark.parametrize("method", ["ntt", "fft_f64"])
+def test_transform_batch_on_branch_streams(ctx, method):
+    # many transform-route problems: they are spread over branch streams that fork
+    # from and join into the caller's stream (run) or become parallel graph branches
+    # (capture); each branch has its own workspace slice
+    g = wl.rng(59 if method == "ntt" else 60)
+    probs = []
+    for k in range(9):
+        h, w = int(g.integers(20, 140)), int(g.integers(20, 160))
+        L = [16, 64, 256][k % 3]
+        f = g.integers(0, L, size=(1, h, w)).astype(np.uint8)
+        se = wl.se_random(g, int(g.integers(1, 12)), int(g.integers(1, 12)), 0.7, int(g.integers(0, 9)))
+        probs.append(wl.Problem(f, L, se, "dilate" if k % 2 else "erode", f"b{k}"))
+    items, outs = _items(probs)
+    ctx.run_batch(items, method=method)
+    ctx.check()
+    for p, (o, c) in zip(probs, outs):
+        _check(p, o, c)
+    for o, c in outs:
+        o.fill_(-99)
+        c.fill_(-99)
+    b = ctx.capture_batch(items, method=method)
+    b.launch()
+    b.launch()
+    ctx.check()
+    for p, (o, c) in zip(probs, outs):
+        _check(p, o, c)
+    b.close()
