@@ -17,7 +17,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("method", ["direct_fp8", "fft_f64"])
+@pytest.mark.parametrize("method", ["direct_fp8", "fft_f64", "ntt"])
 @pytest.mark.parametrize("case", CASES)
 def test_composites_bit_exact(case, method):
     from paper_2305_03018_gb300.morph import get_context

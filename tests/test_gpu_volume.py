@@ -31,7 +31,7 @@ def _case(case):
     return f, L, m, o, origin
 
 
-@pytest.mark.parametrize("method", ["auto", "direct_fp8", "fft_f64"])
+@pytest.mark.parametrize("method", ["auto", "direct_fp8", "fft_f64", "ntt"])
 @pytest.mark.parametrize("case", CASES)
 def test_volume_bit_exact(case, method):
     from paper_2305_03018_gb300.morph import get_context
