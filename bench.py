@@ -599,8 +599,11 @@ def run_config(args, ws, rank, local):
             px += ft.numel()
         res = {}
         outs0 = None
-        for name, method in (("auto", "auto"), ("direct_fp8", "direct_fp8")):
-            bt = ctx.capture_batch(items, method=method)
+        for name, method, tune in (("auto", "auto", False), ("direct_fp8", "direct_fp8", False),
+                                   ("auto_tuned", "auto", True)):
+            t0 = time.perf_counter()
+            bt = ctx.capture_batch(items, method=method, autotune=tune)
+            plan_s = time.perf_counter() - t0
             bt.launch()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -614,7 +617,8 @@ def run_config(args, ws, rank, local):
             snap = [it[4].clone() for it in items]
             exact = outs0 is None or all(bool(torch.equal(a, b2)) for a, b2 in zip(snap, outs0))
             outs0 = outs0 or snap
-            res[name] = {"value": px / (ms * 1e-3) / 1e6, "ms_per_step": ms, "exact_vs_first": exact}
+            res[name] = {"value": px / (ms * 1e-3) / 1e6, "ms_per_step": ms, "exact_vs_first": exact,
+                         "plan_and_capture_s": plan_s}
             bt.close()
         line["config"] = {"workload": "512 uneven problems, sides U[64,1024], L in {16,64,256}, SE 3..63, "
                                       "one captured graph", "pixels": px}

@@ -93,7 +93,10 @@ enum morph_method {
 
 enum morph_flags {
     MORPH_F_ALLOW_UNPROVEN_F32 = 1,  /* run FFT_F32 even where the a-priori bound fails */
-    MORPH_F_VALIDATE = 2             /* FFT routes: measure max |C - rint C| over every degree */
+    MORPH_F_VALIDATE = 2,            /* FFT routes: measure max |C - rint C| over every degree */
+    MORPH_F_AUTOTUNE = 4             /* AUTO: on the first call for a problem key, time each exact
+                                        route the models do not rule out (on the caller's stream and
+                                        output buffers, synchronising it) and keep the fastest */
 };
 
 typedef struct {

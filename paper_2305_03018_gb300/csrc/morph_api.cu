@@ -249,6 +249,8 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
     if (method != MORPH_AUTO) return MORPH_E_INVAL;
     const std::string key = "auto|" + plan_key(f, se, erode, 0);
     if (ctx) {
+        auto tt = ctx->route_cache.find("tuned|" + key);          // a measured choice wins
+        if (tt != ctx->route_cache.end()) { *route = tt->second; return MORPH_OK; }
         auto it = ctx->route_cache.find(key);
         if (it != ctx->route_cache.end()) { *route = it->second; return MORPH_OK; }
     }
@@ -296,12 +298,96 @@ int prepare_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int
     return get_plan(ctx, f, &e.se, erode, route, plan, route == ROUTE_FFT32 && unproven);
 }
 
+static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
+                    const morph_opts* opts, cudaStream_t st);
+
+// Autotuning (MORPH_F_AUTOTUNE with AUTO): time each exact route that the
+// models do not rule out -- FP8 direct, the FP32 FFT where its bound is
+// proven, the NTT (the FP64 FFT only where neither transform route applies)
+// -- once after a warm-up run, on the caller's stream and output buffers
+// (every route writes the same result), and cache the fastest for this
+// problem key.  Routes whose model estimate is more than 8x the best
+// estimate are not timed.  Synchronises the stream; a cached decision is
+// reused by later AUTO calls with or without the flag.
+int tune_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, const morph_opts* opts,
+                 int32_t* out, int32_t* cnt, cudaStream_t st) {
+    int rc = validate(f, b);
+    if (rc) return rc;
+    EffSE e;
+    effective_se(b, erode, &e);
+    const std::string key = "tuned|auto|" + plan_key(f, &e.se, erode, 0);
+    if (ctx->route_cache.count(key)) return MORPH_OK;
+    DirectPlan dp;
+    rc = plan_direct_host(f, &e.se, erode, &dp);
+    if (rc) return rc;
+    if (dp.taps == 0) return MORPH_OK;
+    std::vector<std::pair<int, double>> cand;        // route, model estimate (s)
+    cand.push_back({ROUTE_DIRECT, direct_time(dp, f)});
+    FftPlan fp;
+    const bool f32_ok = plan_fft_tiles(f, &e.se, 4, false, &fp) == MORPH_OK;
+    if (f32_ok) cand.push_back({ROUTE_FFT32, 79e-6 + fp.flop / 2.16e12});
+    NttPlan np;
+    const bool ntt_ok = plan_ntt_tiles(f, &e.se, &np) == MORPH_OK;
+    if (ntt_ok) cand.push_back({ROUTE_NTT, 80e-6 + 1.2 * ntt_time_estimate(np)});
+    if (!f32_ok && !ntt_ok) {
+        FftPlan f64;
+        if (plan_fft_tiles(f, &e.se, 8, false, &f64) == MORPH_OK) cand.push_back({ROUTE_FFT64, 145e-6 + f64.flop / 6.9e11});
+    }
+    double best_est = 1e30;
+    for (const auto& c : cand) best_est = std::min(best_est, c.second);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MORPH_CUDA_TRY(cudaEventCreate(&e0));
+    MORPH_CUDA_TRY(cudaEventCreate(&e1));
+    int best = -1;
+    float best_ms = 0.f;
+    for (const auto& c : cand) {
+        if (c.second > 8.0 * best_est) continue;
+        std::shared_ptr<Plan> plan;
+        rc = get_plan(ctx, f, &e.se, erode, c.first, &plan);
+        if (rc) break;
+        rc = run_plan(ctx, *plan, f, erode, out, cnt, opts, st);         // warm-up (workspace, caches)
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        rc = run_plan(ctx, *plan, f, erode, out, cnt, opts, st);
+        if (rc) break;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = MORPH_E_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best < 0 || ms < best_ms) {
+            best = c.first;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best >= 0) ctx->route_cache[key] = best;
+    return MORPH_OK;
+}
+
 int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
             const morph_opts* opts, cudaStream_t st) {
     if (!out) return inval("null output");
+    int rc = MORPH_OK;
+    if (opts && (opts->flags & MORPH_F_AUTOTUNE) && opts->method == MORPH_AUTO) {
+        rc = tune_problem(ctx, f, b, erode, opts, out, cnt, st);
+        if (rc) return rc;
+    }
     std::shared_ptr<Plan> plan;
-    int rc = prepare_problem(ctx, f, b, erode, opts, &plan);
+    rc = prepare_problem(ctx, f, b, erode, opts, &plan);
     if (rc) return rc;
+    return run_plan(ctx, *plan, f, erode, out, cnt, opts, st);
+}
+
+// Steps 1-3 of one problem with a built plan.
+static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
+                    const morph_opts* opts, cudaStream_t st) {
+    const Plan* plan = &pl;
+    int rc = MORPH_OK;
     const long long npx = static_cast<long long>(f->n) * f->h * f->w;
     if (plan->route == ROUTE_EMPTY) return launch_fill_empty(ctx, out, cnt, npx, erode ? f->L - 1 : 0, st);
     if (plan->route == ROUTE_NTT) return launch_ntt(ctx, plan->ntt, f, erode, out, cnt, st);

@@ -86,7 +86,8 @@ int launch_transform_item(morph_batch* b, int i, uint8_t* ws, cudaStream_t st) {
 }
 
 // Host planning of every problem and the layout of the batch workspace.
-int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts* opts, morph_batch* b) {
+int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts* opts, morph_batch* b,
+                cudaStream_t tune_stream) {
     if (!ctx || (n > 0 && !p) || n < 0) return MORPH_E_INVAL;
     b->ctx = ctx;
     b->items.resize(n);
@@ -98,6 +99,11 @@ int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts*
         it.erode = p[i].op;
         it.out = p[i].out;
         it.cnt = p[i].out_count;
+        if (opts && (opts->flags & MORPH_F_AUTOTUNE) && opts->method == MORPH_AUTO) {
+            // measured route choice on this problem's own buffers (before any capture)
+            int rc = tune_problem(ctx, &p[i].f, &p[i].se, p[i].op, opts, p[i].out, p[i].out_count, tune_stream);
+            if (rc) return rc;
+        }
         int rc = prepare_problem(ctx, &p[i].f, &p[i].se, p[i].op, opts, &it.plan);
         if (rc) return rc;
         if (it.plan->route == ROUTE_DIRECT) b->direct_order.push_back(i);
@@ -267,9 +273,9 @@ int morph_run_batch(morph_ctx* ctx, const morph_problem* p, int n, const morph_o
     if (!ctx) return MORPH_E_INVAL;
     if (n == 0) return MORPH_OK;
     morph_batch b;
-    int rc = batch_setup(ctx, p, n, opts, &b);
-    if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = batch_setup(ctx, p, n, opts, &b, st);
+    if (rc) return rc;
     void* ws = nullptr;
     rc = ctx_workspace(ctx, b.total_bytes, &ws);
     if (rc) return rc;
@@ -285,7 +291,7 @@ int morph_batch_capture(morph_ctx* ctx, const morph_problem* p, int n, const mor
     *out = nullptr;
     morph_batch* b = new (std::nothrow) morph_batch();
     if (!b) return MORPH_E_NOMEM;
-    int rc = batch_setup(ctx, p, n, opts, b);
+    int rc = batch_setup(ctx, p, n, opts, b, nullptr);
     if (rc) {
         delete b;
         return rc;

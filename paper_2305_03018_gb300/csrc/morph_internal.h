@@ -213,6 +213,9 @@ int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, i
 int prepare_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, const morph_opts* opts,
                     std::shared_ptr<Plan>* plan);
 size_t planes_bytes(const morph_image* f);
+// time the exact routes of one AUTO problem on its own buffers and cache the fastest (MORPH_F_AUTOTUNE)
+int tune_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, const morph_opts* opts,
+                 int32_t* out, int32_t* cnt, cudaStream_t st);
 // one dilation (erode = 0) or erosion (erode = 1), the body of morph_dilate / morph_erode
 int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
             const morph_opts* opts, cudaStream_t st);

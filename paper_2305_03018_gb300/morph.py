@@ -23,7 +23,7 @@ MORPH_OK, MORPH_E_INVAL, MORPH_E_RANGE, MORPH_E_NOMEM, MORPH_E_PRECISION, MORPH_
     MORPH_E_UNSUPPORTED = range(8)
 MORPH_U8, MORPH_U16, MORPH_I32 = 0, 1, 2
 MORPH_AUTO, MORPH_DIRECT_FP8, MORPH_FFT_F32, MORPH_FFT_F64, MORPH_NTT = 0, 1, 2, 3, 4
-MORPH_F_ALLOW_UNPROVEN_F32, MORPH_F_VALIDATE = 1, 2
+MORPH_F_ALLOW_UNPROVEN_F32, MORPH_F_VALIDATE, MORPH_F_AUTOTUNE = 1, 2, 4
 METHODS = {"auto": MORPH_AUTO, "direct_fp8": MORPH_DIRECT_FP8, "fft_f32": MORPH_FFT_F32, "fft_f64": MORPH_FFT_F64,
            "ntt": MORPH_NTT}
 
@@ -365,10 +365,11 @@ def se_view(se) -> SEView:
     return SEView(se.mask, se.offset, se.origin)
 
 
-def make_opts(method="auto", allow_unproven_f32=False, validate=False, count_err=None) -> morph_opts:
+def make_opts(method="auto", allow_unproven_f32=False, validate=False, count_err=None, autotune=False) -> morph_opts:
     o = morph_opts()
     o.method = METHODS[method] if isinstance(method, str) else int(method)
-    o.flags = (MORPH_F_ALLOW_UNPROVEN_F32 if allow_unproven_f32 else 0) | (MORPH_F_VALIDATE if validate else 0)
+    o.flags = ((MORPH_F_ALLOW_UNPROVEN_F32 if allow_unproven_f32 else 0) | (MORPH_F_VALIDATE if validate else 0) |
+               (MORPH_F_AUTOTUNE if autotune else 0))
     o.count_err = count_err.data_ptr() if count_err is not None else None
     return o
 
@@ -401,7 +402,7 @@ class Context:
 
     # -- forward -------------------------------------------------------------
     def _run(self, op, f, L, se, method, count, stream, allow_unproven_f32=False, count_err=None, out=None,
-             out_count=None):
+             out_count=None, autotune=False):
         import torch
         img = make_image(f, L)
         sv = se_view(se)
@@ -410,7 +411,7 @@ class Context:
             out = torch.empty(shape, dtype=torch.int32, device=f.device)
         if count and out_count is None:
             out_count = torch.empty(shape, dtype=torch.int32, device=f.device)
-        opts = make_opts(method, allow_unproven_f32, count_err is not None, count_err)
+        opts = make_opts(method, allow_unproven_f32, count_err is not None, count_err, autotune)
         st = stream if stream is not None else current_stream_handle(f.device)
         fn = morph_dilate if op == 0 else morph_erode
         check(fn(self.handle, img, sv.c, out.data_ptr(), out_count.data_ptr() if count else None, opts, st),
@@ -484,15 +485,15 @@ class Context:
             probs.append(pr)
         return probs, keep
 
-    def run_batch(self, items, method="auto", stream=None, allow_unproven_f32=False, count_err=None):
+    def run_batch(self, items, method="auto", stream=None, allow_unproven_f32=False, count_err=None, autotune=False):
         probs, keep = self._problems(items)
-        opts = make_opts(method, allow_unproven_f32, count_err is not None, count_err)
+        opts = make_opts(method, allow_unproven_f32, count_err is not None, count_err, autotune)
         st = stream if stream is not None else current_stream_handle(self.device)
         check(morph_run_batch(self.handle, probs, opts, st), "morph_run_batch")
 
-    def capture_batch(self, items, method="auto", allow_unproven_f32=False):
+    def capture_batch(self, items, method="auto", allow_unproven_f32=False, autotune=False):
         probs, keep = self._problems(items)
-        h = morph_batch_capture(self.handle, probs, make_opts(method, allow_unproven_f32))
+        h = morph_batch_capture(self.handle, probs, make_opts(method, allow_unproven_f32, autotune=autotune))
         return CapturedBatch(h, keep)
 
     def check(self, stream=None):

@@ -121,3 +121,34 @@ def test_transform_batch_on_branch_streams(ctx, method):
     for p, (o, c) in zip(probs, outs):
         _check(p, o, c)
     b.close()
+
+
+def test_autotuned_routes_are_exact_and_cached(ctx):
+    # measured route choice: every timed candidate writes the same exact result,
+    # and the choice is cached for later AUTO calls with or without the flag
+    g = wl.rng(61)
+    cases = [(1, 200, 180, 256, 15, 200), (1, 300, 256, 16, 9, 3), (2, 90, 70, 64, 31, 7)]
+    for (n, h, w, L, k, mo) in cases:
+        f = g.integers(0, L, size=(n, h, w)).astype(np.uint8)
+        se = wl.se_full_random(g, k, mo)
+        ft = torch.from_numpy(f).cuda()
+        out, cnt = ctx.dilate(ft, L, se, method="auto", count=True, autotune=True)
+        ctx.check()
+        D, cD = oracle.dilate(f, L, se.mask, se.offset, se.origin, nthreads=0)
+        assert np.array_equal(out.cpu().numpy(), D) and np.array_equal(cnt.cpu().numpy(), cD)
+        tuned = ctx.plan(ft, L, se, method="auto").method
+        assert tuned in (1, 2, 3, 4)
+        out2 = ctx.dilate(ft, L, se, method="auto")
+        ctx.check()
+        assert np.array_equal(out2.cpu().numpy(), D)
+
+
+def test_autotuned_capture_is_exact(ctx):
+    probs = wl.c5_batch(n=16, seed=62, max_side=200)
+    items, outs = _items(probs)
+    b = ctx.capture_batch(items, method="auto", autotune=True)
+    b.launch()
+    ctx.check()
+    for p, (o, c) in zip(probs, outs):
+        _check(p, o, c)
+    b.close()
