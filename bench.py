@@ -51,7 +51,7 @@ def _args():
     ap.add_argument("--cpu-rows-single", type=int, default=96,
                     help="cpu_baseline: image rows per operation single-threaded")
     ap.add_argument("--ref-rows", type=int, default=128, help="--impl reference: image rows per operation per step")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "x1", "x2", "one"], default="c2",
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "x1", "x2", "x3", "one"], default="c2",
                     help="c2 (default) is the headline workload; the others time the remaining configurations; "
                          "'one' times a single dilation of the sweeps' recipe (--image, --levels, --filter, --method)")
     ap.add_argument("--image", type=int, default=512, help="one: image side")
@@ -635,8 +635,9 @@ def run_sweep(args, ws, rank, local):
     """The paper's runtime experiments on the GPU (Sec. 4.1): x1 = a 512x512
     image with square full-support random filters 32^2..256^2; x2 = n x n
     images with floor(n/10)^2 filters; values randint 0..15 (4-bit) and 0..255
-    (8-bit) for image and filter, as in the paper.  Seconds per dilation for
-    each exact form (forms agree bit for bit)."""
+    (8-bit) for image and filter, as in the paper; x3 = the FPGA experiment's
+    shapes (Sec. 4.2: 28^2 and 1020^2 images, 5x5 filter, 2- to 5-bit tones).
+    Seconds per dilation for each exact form (forms agree bit for bit)."""
     import numpy as np
     import torch
 
@@ -646,10 +647,16 @@ def run_sweep(args, ws, rank, local):
     ctx = get_context(local)
     if args.workload == "x1":
         cases = [(512, k) for k in (32, 64, 128, 256)]
-    else:
+        tonal = ((4, 16), (8, 256))
+    elif args.workload == "x2":
         cases = [(n, n // 10) for n in (128, 256, 512, 1024, 2048, 4096)]
+        tonal = ((4, 16), (8, 256))
+    else:
+        # the FPGA experiment's shapes (Sec. 4.2): 28^2 and 1020^2 images, a 5x5 filter, 2..5-bit tones
+        cases = [(28, 5), (1020, 5)]
+        tonal = ((2, 4), (3, 8), (4, 16), (5, 32))
     rows = []
-    for bits, L in ((4, 16), (8, 256)):
+    for bits, L in tonal:
         for n, k in cases:
             g = wl.rng(1000 * n + k + bits)
             f = torch.from_numpy(wl.uniform_image(g, (1, n, n), L)).cuda()
@@ -751,7 +758,7 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload == "one":
         return run_one(args, ws, rank, local)
-    if args.workload in ("x1", "x2"):
+    if args.workload in ("x1", "x2", "x3"):
         return run_sweep(args, ws, rank, local)
     if args.workload != "c2":
         return run_config(args, ws, rank, local)
