@@ -129,6 +129,15 @@ int morph_ctx_create(int device, morph_ctx **out);
 /* Wait for the context's work, release its device memory and free it. */
 int morph_ctx_destroy(morph_ctx *ctx);
 
+/* Plans (SE blocks, FFT / NTT tables and SE spectra) are cached per context,
+ * keyed by shape, L, SE and route.  The cache holds at most `bytes` of device
+ * memory (default 16 GiB); beyond it the least recently used plans are
+ * dropped (launched work and captured batches keep their own references;
+ * freeing waits for the device as cudaFree does).  Host-only otherwise. */
+int morph_ctx_set_cache_limit(morph_ctx *ctx, size_t bytes);
+/* Device bytes held by the plan cache and the number of cached plans (either nullable). */
+int morph_ctx_cache_info(const morph_ctx *ctx, size_t *bytes, int *nplans);
+
 /* Plan (without running) the dilation (op = 0) or erosion (op = 1) of `f` by
  * `b` under `opts` (nullable = AUTO).  Host-only except for a device query. */
 int morph_plan_query(morph_ctx *ctx, const morph_image *f, const morph_se *b, int op,

@@ -188,11 +188,28 @@ static std::string plan_key(const morph_image* f, const morph_se* se, int erode,
     return k;
 }
 
+static size_t plan_device_bytes(const Plan& p) {
+    if (p.route == ROUTE_DIRECT)
+        return static_cast<size_t>(p.direct.toeplitz_blocks) * 128 * 128 + p.direct.meta.size() * sizeof(int);
+    if (p.route == ROUTE_NTT) {
+        const NttPlan& q = p.ntt;
+        return static_cast<size_t>(q.Rf) * q.ay.N * q.ax.N * sizeof(uint32_t) +
+               (static_cast<size_t>(q.ax.N) + q.ay.N + q.Rf) * sizeof(uint2) + q.Rf * sizeof(uint32_t);
+    }
+    if (p.route == ROUTE_FFT32 || p.route == ROUTE_FFT64) {
+        const FftPlan& q = p.fft;
+        return static_cast<size_t>(q.K) * q.ay.N * q.ax.N * 2 * q.prec +
+               (static_cast<size_t>(q.ax.N) + q.ay.N + q.Rf) * 2 * q.prec;
+    }
+    return 0;
+}
+
 static int get_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, int route,
                     std::shared_ptr<Plan>* out, bool unproven = false) {
     const std::string key = plan_key(f, se, erode, route, unproven);
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
+        it->second->last_use = ++ctx->plan_tick;
         *out = it->second;
         return MORPH_OK;
     }
@@ -214,6 +231,17 @@ static int get_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, in
         int rc = build_fft_plan(ctx, f, se, route == ROUTE_FFT32 ? 4 : 8, unproven, &p->fft);
         if (rc) return rc;
     }
+    p->dev_bytes = plan_device_bytes(*p);
+    p->last_use = ++ctx->plan_tick;
+    // keep the cache within its budget: drop least-recently-used plans
+    while (ctx->plan_bytes + p->dev_bytes > ctx->plan_budget && !ctx->plans.empty()) {
+        auto lru = ctx->plans.begin();
+        for (auto jt = ctx->plans.begin(); jt != ctx->plans.end(); ++jt)
+            if (jt->second->last_use < lru->second->last_use) lru = jt;
+        ctx->plan_bytes -= lru->second->dev_bytes;
+        ctx->plans.erase(lru);
+    }
+    ctx->plan_bytes += p->dev_bytes;
     ctx->plans.emplace(key, p);
     *out = p;
     return MORPH_OK;
@@ -560,6 +588,26 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         out->est_flop = q.flop;
         out->workspace_bytes = q.ws_bytes;
     }
+    return MORPH_OK;
+}
+
+int morph_ctx_set_cache_limit(morph_ctx* ctx, size_t bytes) {
+    if (!ctx) return MORPH_E_INVAL;
+    ctx->plan_budget = bytes;
+    while (ctx->plan_bytes > ctx->plan_budget && !ctx->plans.empty()) {
+        auto lru = ctx->plans.begin();
+        for (auto jt = ctx->plans.begin(); jt != ctx->plans.end(); ++jt)
+            if (jt->second->last_use < lru->second->last_use) lru = jt;
+        ctx->plan_bytes -= lru->second->dev_bytes;
+        ctx->plans.erase(lru);
+    }
+    return MORPH_OK;
+}
+
+int morph_ctx_cache_info(const morph_ctx* ctx, size_t* bytes, int* nplans) {
+    if (!ctx) return MORPH_E_INVAL;
+    if (bytes) *bytes = ctx->plan_bytes;
+    if (nplans) *nplans = static_cast<int>(ctx->plans.size());
     return MORPH_OK;
 }
 

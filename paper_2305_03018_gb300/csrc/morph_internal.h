@@ -153,7 +153,14 @@ struct Plan {
     DirectPlan direct;
     FftPlan fft;
     NttPlan ntt;
+    size_t dev_bytes = 0;         // device memory the plan holds (tables, SE blocks or spectrum)
+    uint64_t last_use = 0;        // context tick of the last lookup (LRU eviction)
 };
+
+// Device memory the context's plan cache may hold before least-recently-used
+// plans are dropped (work already launched, and captured graphs, keep their
+// own references to the plans they use).
+constexpr size_t kPlanCacheBytes = size_t(16) << 30;
 
 }  // namespace morph
 
@@ -178,6 +185,9 @@ struct morph_ctx {
     std::vector<cudaEvent_t> branch_ev;   // their join events
     cudaEvent_t fork_ev = nullptr;
     std::unordered_map<std::string, std::shared_ptr<morph::Plan>> plans;
+    size_t plan_bytes = 0;                // sum of the cached plans' dev_bytes
+    size_t plan_budget = morph::kPlanCacheBytes;
+    uint64_t plan_tick = 0;
     std::unordered_map<std::string, std::shared_ptr<void>> aux_plans;   // backward tap lists, ...
     std::unordered_map<std::string, int> route_cache;                   // AUTO decisions
 };

@@ -105,6 +105,8 @@ _SIGS = {
     "morph_batch_destroy": (ctypes.c_int, [_P]),
     "morph_workspace_size": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), ctypes.c_int,
                                             ctypes.POINTER(morph_opts), ctypes.POINTER(ctypes.c_size_t)]),
+    "morph_ctx_set_cache_limit": (ctypes.c_int, [_P, ctypes.c_size_t]),
+    "morph_ctx_cache_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]),
     "morph_stream_check": (ctypes.c_int, [_P, _P]),
     "morph_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "morph_launch_count": (ctypes.c_uint64, [_P]),
@@ -211,6 +213,17 @@ def morph_dilate_backward(ctx, image, se, d_ptr, cd_ptr, g_ptr, gin_ptr, gse_ptr
 def morph_erode_backward(ctx, image, se, e_ptr, ce_ptr, g_ptr, gin_ptr, gse_ptr, stream) -> int:
     return load_library().morph_erode_backward(ctx, ctypes.byref(image), ctypes.byref(se), e_ptr, ce_ptr, g_ptr,
                                                gin_ptr, gse_ptr, stream)
+
+
+def morph_ctx_set_cache_limit(ctx, nbytes) -> int:
+    return load_library().morph_ctx_set_cache_limit(ctx, int(nbytes))
+
+
+def morph_ctx_cache_info(ctx):
+    """(device bytes held by the plan cache, number of cached plans)."""
+    b, n = ctypes.c_size_t(0), ctypes.c_int(0)
+    check(load_library().morph_ctx_cache_info(ctx, ctypes.byref(b), ctypes.byref(n)), "morph_ctx_cache_info")
+    return int(b.value), int(n.value)
 
 
 def morph_workspace_size(ctx, image, se, op, opts) -> int:
@@ -461,6 +474,14 @@ class Context:
         """Bytes of device workspace: op 0/1 dilation/erosion, 2/3 their backward."""
         sv = se_view(se)                         # keeps the SE arrays alive during the call
         return morph_workspace_size(self.handle, make_image(f, L), sv.c, op, make_opts(method, allow_unproven_f32))
+
+    def set_cache_limit(self, nbytes: int):
+        """Device-memory budget of the plan cache (least recently used plans are dropped beyond it)."""
+        check(morph_ctx_set_cache_limit(self.handle, nbytes), "morph_ctx_set_cache_limit")
+
+    def cache_info(self):
+        """(device bytes held by cached plans, number of plans)."""
+        return morph_ctx_cache_info(self.handle)
 
     def plan(self, f, L, se, op=0, method="auto", allow_unproven_f32=False, **_):
         img = make_image(f, L)

@@ -128,3 +128,25 @@ def test_auto_takes_ntt_for_8bit_offsets_and_stays_exact(ctx):
     ctx.check()
     for rows in [(0, 3), (140, 143), (297, 300)]:
         _eq((out.cpu().numpy(), cnt.cpu().numpy()), _ref(f, 256, se, "dilate", rows=rows), rows=rows)
+
+
+def test_plan_cache_stays_within_its_limit(ctx):
+    # many distinct SEs: least recently used plans are dropped, results stay exact,
+    # and a dropped plan is rebuilt on demand
+    g = wl.rng(95)
+    f = g.integers(0, 256, size=(1, 120, 130)).astype(np.uint8)
+    ft = torch.from_numpy(f).cuda()
+    limit = 24 << 20
+    ctx.set_cache_limit(limit)
+    try:
+        ses = [wl.se_full_random(g, 9, 255) for _ in range(12)]
+        for se in ses:
+            out = ctx.dilate(ft, 256, se, method="ntt")
+            ctx.check()
+            assert ctx.cache_info()[0] <= limit or ctx.cache_info()[1] == 1
+            assert np.array_equal(out.cpu().numpy(), _ref(f, 256, se, "dilate")[0])
+        out = ctx.dilate(ft, 256, ses[0], method="ntt")
+        ctx.check()
+        assert np.array_equal(out.cpu().numpy(), _ref(f, 256, ses[0], "dilate")[0])
+    finally:
+        ctx.set_cache_limit(16 << 30)
