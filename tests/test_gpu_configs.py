@@ -52,3 +52,18 @@ def test_c2_fp64_fft_sampled(ctx):
     D, cD = ctx.dilate(ft, p.L, p.se, method="fft_f64", count=True)
     ctx.check()
     _sampled(p, (D.cpu().numpy(), cD.cpu().numpy()), [(0, 2), (2046, 2048)])
+
+
+@pytest.mark.parametrize("shape,L,k", [((1, 8192, 8192), 16, 5), ((1, 16, 70000), 64, 7), ((3, 2500, 40), 256, 9)])
+def test_large_and_extreme_shapes_sampled(ctx, shape, L, k):
+    # a 67 Mpix image, a very wide strip and tall narrow images through AUTO, checked on sampled rows
+    g = wl.rng(sum(shape) + L)
+    f = g.integers(0, L, size=shape).astype(np.uint8)
+    se = wl.se_random(g, k, k, 0.6, max(1, L // 16))
+    ft = torch.from_numpy(f).cuda()
+    D, cD = ctx.dilate(ft, L, se, method="auto", count=True)
+    ctx.check()
+    H = shape[1]
+    rows = [(0, 2), (H // 2, H // 2 + 1), (H - 2, H)] if H > 4 else [(0, H)]
+    p = wl.Problem(f, L, se, "dilate", "extreme")
+    _sampled(p, (D.cpu().numpy(), cD.cpu().numpy()), rows)

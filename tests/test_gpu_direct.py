@@ -179,3 +179,27 @@ def test_workspace_size_matches_plan_and_is_host_only():
     chunks = 2 * ((200 + (8192 // 300) - 1) // (8192 // 300))
     exp = ((2 * 200 * 300 * 4 + 255) // 256) * 256 + ntaps * chunks * 4
     assert ctx.workspace_size(f, 64, se, op=2) == exp == ctx.workspace_size(f, 64, se, op=3)
+
+
+def test_huge_sparse_offsets():
+    # offsets up to 65535 (R = L + 65535): only the FP8 route applies (its offset
+    # levels are the distinct offsets); the transform routes refuse the size
+    from paper_2305_03018_gb300.morph import MORPH_E_UNSUPPORTED, MorphError, get_context
+    ctx = get_context(0)
+    g = wl.rng(64)
+    f = g.integers(0, 256, size=(1, 70, 90)).astype(np.uint8)
+    m = (g.random((7, 9)) < 0.6).astype(np.uint8)
+    m[3, 4] = 1
+    o = (g.choice([0, 1000, 40000, 65535], size=m.shape) * m).astype(np.int32)
+    se = wl.SE(m, o, (3, 4), "huge")
+    ft = torch.from_numpy(f).cuda()
+    for op in ("dilate", "erode"):
+        fn = ctx.dilate if op == "dilate" else ctx.erode
+        out, cnt = fn(ft, 256, se, method="auto", count=True)
+        ctx.check()
+        ref = (oracle.dilate if op == "dilate" else oracle.erode)(f, 256, m, o, (3, 4))
+        assert np.array_equal(out.cpu().numpy(), ref[0]) and np.array_equal(cnt.cpu().numpy(), ref[1])
+    for method in ("ntt", "fft_f64"):
+        with pytest.raises(MorphError) as ei:
+            ctx.dilate(ft, 256, se, method=method)
+        assert ei.value.status == MORPH_E_UNSUPPORTED

@@ -82,3 +82,15 @@ def test_invalid_requests_are_refused():
     assert lib.morph_workspace_size(None, ctypes.byref(bad), ctypes.byref(sv.c), 0, None, ctypes.byref(bytes_)) \
         == M.MORPH_E_INVAL
     assert lib.morph_workspace_size(None, ctypes.byref(im), ctypes.byref(sv.c), 0, None, None) == M.MORPH_E_INVAL
+
+
+def test_huge_offsets_plan_only_the_fp8_route():
+    m = np.ones((3, 3), np.uint8)
+    o = np.array([[0, 65535, 7], [3, 0, 40000], [1, 2, 3]], np.int32)
+    se = wl.SE(m, o, (1, 1), "huge")
+    im = _img(1, 64, 64, 256)
+    assert _ws(im, se, 0, "auto") == _ws(im, se, 0, "direct_fp8") == 64 * 256 * 64
+    for method in ("ntt", "fft_f64"):
+        with pytest.raises(M.MorphError) as ei:
+            _ws(im, se, 0, method)
+        assert ei.value.status == M.MORPH_E_UNSUPPORTED
