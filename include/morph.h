@@ -88,7 +88,7 @@ enum morph_method {
     MORPH_FFT_F32 = 2,       /* FP32 FFT; refused (E_PRECISION) if the bound fails */
     MORPH_FFT_F64 = 3,       /* FP64 FFT, the plain form of the paper's Step 2 */
     MORPH_NTT = 4            /* number-theoretic transform mod a prime > |B|: exact integer
-                                convolution (Sec. 2.3), no round-off bound needed */
+                                convolution (Sec. 2.2), no round-off bound needed */
 };
 
 enum morph_flags {

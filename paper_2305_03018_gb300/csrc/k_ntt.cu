@@ -1,6 +1,6 @@
 // Step 2 of the method as an exact number-theoretic transform (NTT), followed
 // by Step 3 (Eq. 9).  The paper points to modular transforms as the exact
-// alternative to the floating-point FFT (Sec. 2.3): the count polynomial of
+// alternative to the floating-point FFT (Sec. 2.2): the count polynomial of
 // Eq. Obs7 has integer coefficients in [0, |B|], so its convolution computed
 // modulo a prime P > |B| is the exact count, with no round-off bound.
 //
