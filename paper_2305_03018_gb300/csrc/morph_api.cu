@@ -307,7 +307,10 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
         }
     }
     (void)unproven;
-    if (ctx) ctx->route_cache.emplace(key, *route);
+    if (ctx) {
+        if (ctx->route_cache.size() >= kRouteCacheEntries) ctx->route_cache.clear();   // keys hold whole SEs
+        ctx->route_cache.emplace(key, *route);
+    }
     return MORPH_OK;
 }
 
@@ -393,7 +396,10 @@ int tune_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int er
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    if (best >= 0) ctx->route_cache[key] = best;
+    if (best >= 0) {
+        if (ctx->route_cache.size() >= kRouteCacheEntries) ctx->route_cache.clear();
+        ctx->route_cache[key] = best;
+    }
     return MORPH_OK;
 }
 

@@ -161,6 +161,9 @@ struct Plan {
 // plans are dropped (work already launched, and captured graphs, keep their
 // own references to the plans they use).
 constexpr size_t kPlanCacheBytes = size_t(16) << 30;
+// AUTO decisions kept per context (host memory: each key holds the SE); the
+// table is cleared when full, and decisions are recomputed on demand.
+constexpr size_t kRouteCacheEntries = 4096;
 
 }  // namespace morph
 
