@@ -62,6 +62,7 @@ def _args():
                     help="one: full-support square, convex-hull support (as C3) or flat disk")
     ap.add_argument("--max-off", type=int, default=-1, help="one: largest SE offset (default L - 1)")
     ap.add_argument("--smooth", action="store_true", help="one: Gaussian-blurred image (as C3) instead of uniform")
+    ap.add_argument("--unproven", action="store_true", help="one: allow the FP32 FFT where its bound is not proven")
     return ap.parse_args()
 
 
@@ -716,16 +717,17 @@ def run_one(args, ws, rank, local):
         se = wl.se_flat_disk(k // 2)
     else:
         se = wl.se_full_random(g, k, mo)
-    info = ctx.plan(f, L, se, method=args.method)
+    kw = {"allow_unproven_f32": True} if args.unproven else {}
+    info = ctx.plan(f, L, se, method=args.method, **kw)
     out = torch.empty((1, n, n), dtype=torch.int32, device="cuda")
     for _ in range(max(1, args.warmup)):
-        ctx.dilate(f, L, se, method=args.method, out=out)
+        ctx.dilate(f, L, se, method=args.method, out=out, **kw)
     torch.cuda.synchronize()
     ctx.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(max(1, args.steps)):
-        ctx.dilate(f, L, se, method=args.method, out=out)
+        ctx.dilate(f, L, se, method=args.method, out=out, **kw)
     e1.record()
     torch.cuda.synchronize()
     kt = ctx.profile_read()

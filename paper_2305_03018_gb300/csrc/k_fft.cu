@@ -120,21 +120,30 @@ __device__ __forceinline__ void dft5(cT* v) {
 constexpr int kFftMaxStages = 16;   // FftAxis::rad capacity
 constexpr int kFftMaxN = 2048;
 
-// One Stockham stage of radix R for `batch` interleaved transforms of length N
-// (element p of transform c at index p * batch + c), forward direction.
-template <typename T, typename cT, int R>
+constexpr int fft_ilog2(int b) { return b <= 1 ? 0 : 1 + fft_ilog2(b / 2); }
+// element p of transform c of a batch of B interleaved transforms lives at
+// p * pitch(B) + c; the odd pitch keeps column reads (fixed c, consecutive p)
+// free of bank conflicts
+constexpr int fpitch(int B) { return B == 1 ? 1 : B + 1; }
+
+// One Stockham stage of radix R over B interleaved transforms of length N,
+// forward direction; tw[m] = exp(-2 pi i m / N).  j / Ns by a precomputed
+// magic multiplier (exact for j Ns < 2^32).
+template <typename T, typename cT, int R, int B>
 __device__ __forceinline__ void stockham_stage(const cT* __restrict__ x, cT* __restrict__ y, int N, int Ns,
-                                               const cT* __restrict__ tw, int batch) {
+                                               uint32_t nsm, int tstep, const cT* __restrict__ tw) {
+    constexpr int PB = fpitch(B);
+    constexpr int LB = fft_ilog2(B);
     const int M = N / R;
-    const int total = M * batch;
-    const int tstep = N / (Ns * R);
+    const int total = M * B;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int c = t % batch;
-        const int j = t / batch;
-        const int k = j % Ns;
+        const int c = t & (B - 1);
+        const int j = t >> LB;
+        const int g = Ns == 1 ? j : static_cast<int>(__umulhi(static_cast<uint32_t>(j), nsm));
+        const int k = j - g * Ns;
         cT v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = x[(j + r * M) * batch + c];
+        for (int r = 0; r < R; ++r) v[r] = x[(j + r * M) * PB + c];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * tstep]);
@@ -143,23 +152,23 @@ __device__ __forceinline__ void stockham_stage(const cT* __restrict__ x, cT* __r
         if (R == 3) dft3<T, cT>(v);
         if (R == 4) dft4<T, cT>(v);
         if (R == 5) dft5<T, cT>(v);
-        const int d = (j / Ns) * Ns * R + k;
+        const int d = g * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) y[(d + r * Ns) * batch + c] = v[r];
+        for (int r = 0; r < R; ++r) y[(d + r * Ns) * PB + c] = v[r];
     }
 }
 
-// Forward FFT of `batch` interleaved transforms held in a (ping) with scratch
-// b (pong); returns the buffer holding the result.  Block-wide.
-template <typename T, typename cT>
-__device__ cT* fft_block(cT* a, cT* b, const FftAxis& ax, const cT* tw, int batch) {
+// Forward FFT of B interleaved transforms held in a (scratch b); returns the
+// buffer holding the result.  Block-wide; ends with a barrier.
+template <typename T, typename cT, int B>
+__device__ __forceinline__ cT* fft_block(cT* a, cT* b, const FftAxis& ax, const cT* tw) {
     int Ns = 1;
     for (int s = 0; s < ax.nst; ++s) {
         const int R = ax.rad[s];
-        if (R == 4) stockham_stage<T, cT, 4>(a, b, ax.N, Ns, tw, batch);
-        else if (R == 2) stockham_stage<T, cT, 2>(a, b, ax.N, Ns, tw, batch);
-        else if (R == 3) stockham_stage<T, cT, 3>(a, b, ax.N, Ns, tw, batch);
-        else stockham_stage<T, cT, 5>(a, b, ax.N, Ns, tw, batch);
+        if (R == 4) stockham_stage<T, cT, 4, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
+        else if (R == 2) stockham_stage<T, cT, 2, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
+        else if (R == 3) stockham_stage<T, cT, 3, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
+        else stockham_stage<T, cT, 5, B>(a, b, ax.N, Ns, ax.nsm[s], ax.tstep[s], tw);
         __syncthreads();
         Ns *= R;
         cT* t = a;
@@ -178,6 +187,7 @@ struct FftArgs {
     // method
     int R, K;                 // degrees, grey frequencies (Rf/2 + 1)
     int Rf;                   // grey-axis DFT length (smooth, >= R)
+    uint32_t rfm;             // ceil(2^32 / Rf): e mod Rf by a multiply for e < 2^21
     FftAxis ar;               // its factorisation
     int To_y, To_x, Rin_y, Win_x;   // output tile, input tile (To + k - 1)
     int ry, rx;               // SE reach below / right: kh - 1 - oy, kw - 1 - ox
@@ -215,15 +225,18 @@ __device__ __forceinline__ void tile_origin(const FftArgs& a, long long gt, int*
     *x0 = (rem % a.tiles_x) * a.To_x;
 }
 
-template <typename T>
+// grid (Rin_y, wave_tiles): input row rho of tile tl; the K grey frequencies
+// B at a time (B interleaved row transforms per pass)
+template <typename T, int B>
 __global__ void __launch_bounds__(256) k_fft_rows_fwd(const FftArgs a) {
     using cT = typename CxT<T>::type;
+    constexpr int PB = fpitch(B);
     extern __shared__ __align__(16) unsigned char sm[];
     const int Nx = a.ax.N;
     cT* tw = reinterpret_cast<cT*>(sm);
     cT* b0 = tw + Nx;
-    cT* b1 = b0 + Nx;
-    int* lev = reinterpret_cast<int*>(b1 + Nx);
+    cT* b1 = b0 + Nx * PB;
+    int* lev = reinterpret_cast<int*>(b1 + Nx * PB);
     const cT* gtw = static_cast<const cT*>(a.tw_x);
     const cT* wr = static_cast<const cT*>(a.wr);
     const int rho = blockIdx.x;                 // input row of the tile
@@ -233,10 +246,10 @@ __global__ void __launch_bounds__(256) k_fft_rows_fwd(const FftArgs a) {
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) tw[j] = gtw[j];
     const int iy = y0 - a.ry + rho;
     bool bad = false;
-    for (int p = threadIdx.x; p < a.Win_x; p += blockDim.x) {
+    for (int p = threadIdx.x; p < Nx; p += blockDim.x) {
         const int ix = x0 - a.rx + p;
         int v = -1;
-        if (iy >= 0 && iy < a.h && ix >= 0 && ix < a.w) {
+        if (p < a.Win_x && iy >= 0 && iy < a.h && ix >= 0 && ix < a.w) {
             const int f = fft_load_px(a.src, a.dtype, n * a.batch_stride + iy * a.row_stride + ix);
             if (f < 0 || f >= a.L) bad = true;
             else v = a.flip ? a.L - 1 - f : f;
@@ -247,79 +260,106 @@ __global__ void __launch_bounds__(256) k_fft_rows_fwd(const FftArgs a) {
     __syncthreads();
     if (a.tilemax) {
         int mx = -1;
-        for (int p = threadIdx.x; p < a.Win_x; p += blockDim.x) mx = max(mx, lev[p]);
+        for (int p = threadIdx.x; p < Nx; p += blockDim.x) mx = max(mx, lev[p]);
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if ((threadIdx.x & 31) == 0 && mx >= 0) atomicMax(a.tilemax + tl, mx);
     }
-    cT* dst = static_cast<cT*>(a.buf);
-    for (int k = 0; k < a.K; ++k) {
-        for (int p = threadIdx.x; p < Nx; p += blockDim.x) {
+    const long long plane = static_cast<long long>(a.ay.N) * Nx;
+    cT* dst = static_cast<cT*>(a.buf) + static_cast<long long>(tl) * a.K * plane + static_cast<long long>(rho) * Nx;
+    for (int k0 = 0; k0 < a.K; k0 += B) {
+        for (int t = threadIdx.x; t < B * Nx; t += blockDim.x) {
+            const int c = t & (B - 1), p = t >> fft_ilog2(B);
+            const int l = lev[p];
             cT v = cx<cT>(0, 0);
-            if (p < a.Win_x && lev[p] >= 0) v = wr[(static_cast<long long>(k) * lev[p]) % a.Rf];
-            b0[p] = v;
+            if (l >= 0 && k0 + c < a.K) {
+                const uint32_t e = static_cast<uint32_t>((k0 + c) * l);
+                v = wr[e - __umulhi(e, a.rfm) * static_cast<uint32_t>(a.Rf)];       // e mod Rf
+            }
+            b0[p * PB + c] = v;
         }
         __syncthreads();
-        const cT* res = fft_block<T, cT>(b0, b1, a.ax, tw, 1);
-        cT* row = dst + ((static_cast<long long>(tl) * a.K + k) * a.ay.N + rho) * Nx;
-        for (int p = threadIdx.x; p < Nx; p += blockDim.x) row[p] = res[p];
+        const cT* res = fft_block<T, cT, B>(b0, b1, a.ax, tw);
+        const int kb = min(B, a.K - k0);
+        for (int c = 0; c < kb; ++c)
+            for (int p = threadIdx.x; p < Nx; p += blockDim.x) dst[(k0 + c) * plane + p] = res[p * PB + c];
         __syncthreads();
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_fft_cols(const FftArgs a) {
+// grid (wave_tiles, ceil(Nx / C), K): column FFT of C columns, multiply by the
+// SE spectrum, inverse column FFT (conjugate, forward, conjugate), keep the
+// output rows.  The tiles of one (column group, k) run together and share
+// that strip of the SE spectrum through L2.
+template <typename T, int C>
+__global__ void __launch_bounds__(512) k_fft_cols(const FftArgs a) {
     using cT = typename CxT<T>::type;
+    constexpr int PC = fpitch(C);
     extern __shared__ __align__(16) unsigned char sm[];
-    const int Ny = a.ay.N, Nx = a.ax.N, C = a.colgroup;
+    const int Ny = a.ay.N, Nx = a.ax.N;
     cT* tw = reinterpret_cast<cT*>(sm);
     cT* b0 = tw + Ny;
-    cT* b1 = b0 + Ny * C;
+    cT* b1 = b0 + Ny * PC;
     const cT* gtw = static_cast<const cT*>(a.tw_y);
-    const int u0 = blockIdx.x * C;
-    const int k = blockIdx.y;
-    const int tl = blockIdx.z;
+    const int tl = blockIdx.x, u0 = blockIdx.y * C, k = blockIdx.z;
     for (int j = threadIdx.x; j < Ny; j += blockDim.x) tw[j] = gtw[j];
     cT* plane = static_cast<cT*>(a.buf) + (static_cast<long long>(tl) * a.K + k) * Ny * Nx;
     for (int t = threadIdx.x; t < Ny * C; t += blockDim.x) {
-        const int c = t % C, rho = t / C;
-        b0[t] = (rho < a.Rin_y && u0 + c < Nx) ? plane[static_cast<long long>(rho) * Nx + u0 + c] : cx<cT>(0, 0);
+        const int c = t & (C - 1), rho = t >> fft_ilog2(C);
+        b0[rho * PC + c] = (rho < a.Rin_y && u0 + c < Nx) ? plane[static_cast<long long>(rho) * Nx + u0 + c]
+                                                          : cx<cT>(0, 0);
     }
     __syncthreads();
-    cT* res = fft_block<T, cT>(b0, b1, a.ay, tw, C);
+    cT* res = fft_block<T, cT, C>(b0, b1, a.ay, tw);
     cT* other = (res == b0) ? b1 : b0;
     const cT* S = static_cast<const cT*>(a.S) + static_cast<long long>(k) * Ny * Nx;
     // multiply by the SE spectrum, conjugate for the inverse transform
     for (int t = threadIdx.x; t < Ny * C; t += blockDim.x) {
-        const int c = t % C, v = t / C;
-        if (u0 + c < Nx) res[t] = cconj(cmul(res[t], S[static_cast<long long>(v) * Nx + u0 + c]));
+        const int c = t & (C - 1), v = t >> fft_ilog2(C);
+        if (u0 + c < Nx) res[v * PC + c] = cconj(cmul(res[v * PC + c], S[static_cast<long long>(v) * Nx + u0 + c]));
     }
     __syncthreads();
-    const cT* out = fft_block<T, cT>(res, other, a.ay, tw, C);
+    const cT* out = fft_block<T, cT, C>(res, other, a.ay, tw);
+    // torus position of output row q is (q + ry) mod Ny (ry < 0 or >= Ny when the origin lies outside the box)
+    const int base = ((a.ry % Ny) + Ny) % Ny;
     for (int t = threadIdx.x; t < a.To_y * C; t += blockDim.x) {
-        const int c = t % C, q = t / C;
-        // torus position of output row q is (q + ry) mod Ny (ry < 0 or >= Ny when the origin lies outside the box)
-        const int pos = ((q + a.ry) % Ny + Ny) % Ny;
-        if (u0 + c < Nx) plane[static_cast<long long>(q) * Nx + u0 + c] = cconj(out[pos * C + c]);
+        const int c = t & (C - 1), q = t >> fft_ilog2(C);
+        int pos = base + q;
+        if (pos >= Ny) pos -= Ny;
+        if (u0 + c < Nx) plane[static_cast<long long>(q) * Nx + u0 + c] = cconj(out[pos * PC + c]);
     }
 }
 
-template <typename T>
+// grid (To_y, ceil(K / B), wave_tiles): inverse row FFT of output row q for B
+// grey frequencies, keep the output columns
+template <typename T, int B>
 __global__ void __launch_bounds__(256) k_fft_rows_inv(const FftArgs a) {
     using cT = typename CxT<T>::type;
+    constexpr int PB = fpitch(B);
     extern __shared__ __align__(16) unsigned char sm[];
     const int Nx = a.ax.N;
     cT* tw = reinterpret_cast<cT*>(sm);
     cT* b0 = tw + Nx;
-    cT* b1 = b0 + Nx;
+    cT* b1 = b0 + Nx * PB;
     const cT* gtw = static_cast<const cT*>(a.tw_x);
-    const int q = blockIdx.x, k = blockIdx.y, tl = blockIdx.z;
+    const int q = blockIdx.x, k0 = blockIdx.y * B, tl = blockIdx.z;
+    const int kb = min(B, a.K - k0);
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) tw[j] = gtw[j];
-    cT* row = static_cast<cT*>(a.buf) + ((static_cast<long long>(tl) * a.K + k) * a.ay.N + q) * Nx;
-    for (int p = threadIdx.x; p < Nx; p += blockDim.x) b0[p] = cconj(row[p]);
+    const long long plane = static_cast<long long>(a.ay.N) * Nx;
+    cT* rows = static_cast<cT*>(a.buf) + (static_cast<long long>(tl) * a.K + k0) * plane + static_cast<long long>(q) * Nx;
+    for (int c = 0; c < B; ++c)
+        for (int p = threadIdx.x; p < Nx; p += blockDim.x)
+            b0[p * PB + c] = c < kb ? cconj(rows[c * plane + p]) : cx<cT>(0, 0);
     __syncthreads();
-    const cT* res = fft_block<T, cT>(b0, b1, a.ax, tw, 1);
-    for (int p = threadIdx.x; p < a.To_x; p += blockDim.x) row[p] = cconj(res[((p + a.rx) % Nx + Nx) % Nx]);
+    const cT* res = fft_block<T, cT, B>(b0, b1, a.ax, tw);
+    const int base = ((a.rx % Nx) + Nx) % Nx;
+    for (int c = 0; c < kb; ++c)
+        for (int p = threadIdx.x; p < a.To_x; p += blockDim.x) {
+            int pos = base + p;
+            if (pos >= Nx) pos -= Nx;
+            rows[c * plane + p] = cconj(res[pos * PB + c]);
+        }
 }
+
 
 // Step 3 by direct evaluation, for grey axes short enough that a few
 // evaluations per pixel beat a transform: C(x, d) = (1 / (Rf Nx Ny))
@@ -382,19 +422,20 @@ __global__ void __launch_bounds__(256) k_fft_scan(const FftArgs a) {
     }
 }
 
-// Grey-axis inverse FFT + Step 3 for `pixgroup` consecutive output pixels of
-// one tile row: C(x, d) = (1 / (Rf Nx Ny)) sum_k c_k(x) exp(2 pi i k d / Rf)
-// with c_{Rf-k} = conj(c_k); then each warp scans its pixels' degrees from
-// R - 1 downward in chunks of 32 (ballot), keeping the top d with
-// rint(C) >= 1 and its count.
-template <typename T>
-__global__ void __launch_bounds__(256) k_fft_range(const FftArgs a) {
+// grid (ceil(To_x / C), To_y, wave_tiles): grey-axis inverse FFT + Step 3 for
+// C consecutive output pixels of one tile row: C(x, d) = (1 / (Rf Nx Ny))
+// sum_k c_k(x) exp(2 pi i k d / Rf) with c_{Rf-k} = conj(c_k); then each warp
+// scans its pixels' degrees from R - 1 downward in chunks of 32 (ballot),
+// keeping the top d with rint(C) >= 1 and its count.
+template <typename T, int C>
+__global__ void __launch_bounds__(512) k_fft_range(const FftArgs a) {
     using cT = typename CxT<T>::type;
+    constexpr int PC = fpitch(C);
     extern __shared__ __align__(16) unsigned char sm[];
-    const int Rf = a.ar.N, C = a.pixgroup, Nx = a.ax.N, Ny = a.ay.N;
+    const int Rf = a.ar.N, Nx = a.ax.N, Ny = a.ay.N;
     cT* tw = reinterpret_cast<cT*>(sm);
     cT* b0 = tw + Rf;
-    cT* b1 = b0 + Rf * C;
+    cT* b1 = b0 + Rf * PC;
     const cT* gtw = static_cast<const cT*>(a.wr);
     const int x0 = blockIdx.x * C, q = blockIdx.y, tl = blockIdx.z;
     int n, y0, tx0;
@@ -404,17 +445,17 @@ __global__ void __launch_bounds__(256) k_fft_range(const FftArgs a) {
     const long long kstride = static_cast<long long>(Ny) * Nx;
     // Hermitian extension, conjugated for the inverse transform
     for (int t = threadIdx.x; t < Rf * C; t += blockDim.x) {
-        const int c = t % C, k = t / C;
+        const int c = t & (C - 1), k = t >> fft_ilog2(C);
         const int xo = x0 + c;
         cT v = cx<cT>(0, 0);
         if (xo < a.To_x) {
             if (k < a.K) v = cconj(base[k * kstride + xo]);
             else v = base[(Rf - k) * kstride + xo];
         }
-        b0[t] = v;
+        b0[k * PC + c] = v;
     }
     __syncthreads();
-    const cT* res = fft_block<T, cT>(b0, b1, a.ar, tw, C);
+    const cT* res = fft_block<T, cT, C>(b0, b1, a.ar, tw);
     const T scale = static_cast<T>(1.0) / (static_cast<T>(Rf) * static_cast<T>(Nx) * static_cast<T>(Ny));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     float emax = 0.f;
@@ -428,7 +469,7 @@ __global__ void __launch_bounds__(256) k_fft_range(const FftArgs a) {
             T Cv = 0;
             bool hit = false;
             if (d < a.R) {
-                Cv = res[d * C + c].x * scale;          // real part of the conjugated result
+                Cv = res[d * PC + c].x * scale;          // real part of the conjugated result
                 const T rc = rint(Cv);
                 if (a.validate || D < 0) emax = fmaxf(emax, static_cast<float>(fabs(Cv - rc)));
                 hit = rc >= static_cast<T>(1);
@@ -498,25 +539,32 @@ __global__ void __launch_bounds__(256) k_plane_rows(double2* planes, FftAxis ax,
     double2* p = planes + (static_cast<long long>(k) * Ny + row) * Nx;
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) b0[j] = p[j];
     __syncthreads();
-    const double2* res = fft_block<double, double2>(b0, b1, ax, tw, 1);
+    const double2* res = fft_block<double, double2, 1>(b0, b1, ax, tw);
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) p[j] = res[j];
 }
 
-__global__ void __launch_bounds__(256) k_plane_cols(double2* planes, FftAxis ay, const double2* gtw, int Nx, int C) {
+constexpr int kPlaneCols = 4;   // columns per CTA of k_plane_cols
+
+__global__ void __launch_bounds__(256) k_plane_cols(double2* planes, FftAxis ay, const double2* gtw, int Nx) {
+    constexpr int C = kPlaneCols, PC = fpitch(C);
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = ay.N;
     double2* tw = reinterpret_cast<double2*>(sm);
     double2* b0 = tw + Ny;
-    double2* b1 = b0 + Ny * C;
+    double2* b1 = b0 + Ny * PC;
     const int u0 = blockIdx.x * C, k = blockIdx.y;
     for (int j = threadIdx.x; j < Ny; j += blockDim.x) tw[j] = gtw[j];
     double2* p = planes + static_cast<long long>(k) * Ny * Nx;
-    for (int t = threadIdx.x; t < Ny * C; t += blockDim.x)
-        b0[t] = (u0 + t % C < Nx) ? p[static_cast<long long>(t / C) * Nx + u0 + t % C] : make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < Ny * C; t += blockDim.x) {
+        const int c = t & (C - 1), r = t >> fft_ilog2(C);
+        b0[r * PC + c] = (u0 + c < Nx) ? p[static_cast<long long>(r) * Nx + u0 + c] : make_double2(0.0, 0.0);
+    }
     __syncthreads();
-    const double2* res = fft_block<double, double2>(b0, b1, ay, tw, C);
-    for (int t = threadIdx.x; t < Ny * C; t += blockDim.x)
-        if (u0 + t % C < Nx) p[static_cast<long long>(t / C) * Nx + u0 + t % C] = res[t];
+    const double2* res = fft_block<double, double2, C>(b0, b1, ay, tw);
+    for (int t = threadIdx.x; t < Ny * C; t += blockDim.x) {
+        const int c = t & (C - 1), r = t >> fft_ilog2(C);
+        if (u0 + c < Nx) p[static_cast<long long>(r) * Nx + u0 + c] = res[r * PC + c];
+    }
 }
 
 __global__ void k_to_float2(const double2* __restrict__ s, float2* __restrict__ d, long long n) {
@@ -545,7 +593,15 @@ static bool factor_axis(int N, FftAxis* ax) {
         }
         return true;
     };
-    return push(4, f4) && push(2, f2) && push(3, f3) && push(5, f5);
+    if (!(push(4, f4) && push(2, f2) && push(3, f3) && push(5, f5))) return false;
+    int Ns = 1;
+    for (int st = 0; st < ax->nst; ++st) {
+        ax->tstep[st] = N / (Ns * ax->rad[st]);
+        // ceil(2^32 / Ns): floor(j * nsm / 2^32) = j / Ns exactly while j * Ns < 2^32
+        ax->nsm[st] = Ns == 1 ? 0u : static_cast<uint32_t>(((uint64_t(1) << 32) + Ns - 1) / Ns);
+        Ns *= ax->rad[st];
+    }
+    return true;
 }
 
 static int smooth_at_least(int n) {
@@ -585,8 +641,19 @@ FftPlan::~FftPlan() {
         if (q) cudaFree(q);
 }
 
-static size_t smem_rows(int N, int prec) { return static_cast<size_t>(3) * N * 2 * prec + 4 * static_cast<size_t>(N); }
-static size_t smem_cols(int N, int C, int prec) { return static_cast<size_t>(N) * (1 + 2 * C) * 2 * prec; }
+// shared memory (bytes): twiddles + two pitched buffers of B transforms (+ row levels)
+static size_t smem_rows(int N, int B, int prec) {
+    return static_cast<size_t>(N) * 2 * prec * (1 + 2 * fpitch(B)) + 4 * static_cast<size_t>(N);
+}
+static size_t smem_cols(int N, int C, int prec) { return static_cast<size_t>(N) * 2 * prec * (1 + 2 * fpitch(C)); }
+constexpr size_t kFftSmemHalf = 110 * 1024;     // two CTAs per SM
+constexpr size_t kFftSmemQuarter = 56 * 1024;   // four CTAs per SM
+
+static int fft_pow2_floor(int x) {
+    int p = 1;
+    while (p * 2 <= x) p *= 2;
+    return p;
+}
 
 static double axis_flop(const FftAxis& a) {
     double lg = 0;
@@ -657,10 +724,18 @@ int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unpr
     p->Win_x = p->To_x + kw - 1;
     p->ntiles = static_cast<long long>(f->n) * p->tiles_y * p->tiles_x;
     p->flop = best + static_cast<double>(f->n) * f->h * f->w * axis_flop(p->ar);
-    p->colgroup = prec == 4 ? 4 : 2;
-    // pixels per k_fft_range CTA: two Rf-point buffers per pixel within ~160 KB
-    p->pixgroup = static_cast<int>(std::min<size_t>(32, std::max<size_t>(1, (160u * 1024u) /
-                                                                                (2u * p->Rf * 2u * prec))));
+    // batches (powers of two): ~4096 elements per row-kernel pass, no more
+    // frequencies than there are, row and column groups sized for four CTAs per
+    // SM (the complex elements are 8 or 16 bytes), pixel groups for two
+    p->kgroup = std::min(32, fft_pow2_floor(std::max(1, 4096 / p->ax.N)));
+    while (p->kgroup > 1 && p->kgroup / 2 >= p->K) p->kgroup /= 2;
+    while (p->kgroup > 1 && smem_rows(p->ax.N, p->kgroup, prec) > kFftSmemQuarter) p->kgroup /= 2;
+    p->colgroup = 16;
+    while (p->colgroup > 1 && smem_cols(p->ay.N, p->colgroup, prec) > kFftSmemQuarter) p->colgroup /= 2;
+    p->pixgroup = 32;
+    while (p->pixgroup > 1 && smem_cols(p->Rf, p->pixgroup, prec) > kFftSmemHalf) p->pixgroup /= 2;
+    p->col_threads = p->ay.N * p->colgroup >= 8192 ? 512 : 256;
+    p->pix_threads = p->Rf * p->pixgroup >= 8192 ? 512 : 256;
     const size_t per_tile = static_cast<size_t>(p->K) * p->ax.N * p->ay.N * 2 * prec;
     const size_t budget = size_t(4) << 30;
     long long wt = static_cast<long long>(budget / std::max<size_t>(per_tile, 1));
@@ -676,17 +751,63 @@ int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unpr
     return MORPH_OK;
 }
 
+typedef void (*FftKernel)(const FftArgs);
+
 template <typename T>
-static int set_fft_smem(size_t rows, size_t cols) {
+static FftKernel rows_fwd_for(int B) {
+    switch (B) {
+        case 1: return k_fft_rows_fwd<T, 1>;
+        case 2: return k_fft_rows_fwd<T, 2>;
+        case 4: return k_fft_rows_fwd<T, 4>;
+        case 8: return k_fft_rows_fwd<T, 8>;
+        case 16: return k_fft_rows_fwd<T, 16>;
+        default: return k_fft_rows_fwd<T, 32>;
+    }
+}
+template <typename T>
+static FftKernel rows_inv_for(int B) {
+    switch (B) {
+        case 1: return k_fft_rows_inv<T, 1>;
+        case 2: return k_fft_rows_inv<T, 2>;
+        case 4: return k_fft_rows_inv<T, 4>;
+        case 8: return k_fft_rows_inv<T, 8>;
+        case 16: return k_fft_rows_inv<T, 16>;
+        default: return k_fft_rows_inv<T, 32>;
+    }
+}
+template <typename T>
+static FftKernel cols_for(int C) {
+    switch (C) {
+        case 1: return k_fft_cols<T, 1>;
+        case 2: return k_fft_cols<T, 2>;
+        case 4: return k_fft_cols<T, 4>;
+        case 8: return k_fft_cols<T, 8>;
+        default: return k_fft_cols<T, 16>;
+    }
+}
+template <typename T>
+static FftKernel range_for(int C) {
+    switch (C) {
+        case 1: return k_fft_range<T, 1>;
+        case 2: return k_fft_range<T, 2>;
+        case 4: return k_fft_range<T, 4>;
+        case 8: return k_fft_range<T, 8>;
+        case 16: return k_fft_range<T, 16>;
+        default: return k_fft_range<T, 32>;
+    }
+}
+
+template <typename T>
+static int set_fft_smem() {
     static bool done = false;
     if (done) return MORPH_OK;
     const int big = 200 * 1024;
-    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_fft_range<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    (void)rows;
-    (void)cols;
+    for (int b = 1; b <= 32; b *= 2) {
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(rows_fwd_for<T>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(rows_inv_for<T>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(range_for<T>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+        if (b <= 16) MORPH_CUDA_TRY(cudaFuncSetAttribute(cols_for<T>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    }
     done = true;
     return MORPH_OK;
 }
@@ -709,8 +830,8 @@ int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int
     const int Nx = p->ax.N, Ny = p->ay.N, K = p->K, Rf = p->Rf;
     rc = set_plane_smem();
     if (rc) return rc;
-    if (prec == 4) rc = set_fft_smem<float>(0, 0);
-    else rc = set_fft_smem<double>(0, 0);
+    if (prec == 4) rc = set_fft_smem<float>();
+    else rc = set_fft_smem<double>();
     if (rc) return rc;
     const size_t cbytes = 2 * static_cast<size_t>(prec);
     MORPH_CUDA_TRY(cudaMalloc(&p->tw_x, Nx * cbytes));
@@ -752,9 +873,9 @@ int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int
         const unsigned blocks = static_cast<unsigned>(std::min<long long>((n + 255) / 256, 4096));
         k_se_scatter<<<blocks, 256>>>(s64, K, Ny, Nx, d_taps, static_cast<int>(taps.size()), Rf);
     }
-    k_plane_rows<<<dim3(Ny, K), 256, smem_rows(Nx, 8)>>>(s64, p->ax, tw64x, Ny);
-    const int C64 = 2;
-    k_plane_cols<<<dim3((Nx + C64 - 1) / C64, K), 256, smem_cols(Ny, C64, 8)>>>(s64, p->ay, tw64y, Nx, C64);
+    k_plane_rows<<<dim3(Ny, K), 256, smem_rows(Nx, 1, 8)>>>(s64, p->ax, tw64x, Ny);
+    k_plane_cols<<<dim3((Nx + kPlaneCols - 1) / kPlaneCols, K), 256, smem_cols(Ny, kPlaneCols, 8)>>>(s64, p->ay,
+                                                                                                     tw64y, Nx);
     ctx->launches += 5;
     MORPH_CUDA_TRY(cudaGetLastError());
     if (prec == 4) {
@@ -794,6 +915,7 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
     a.R = p.R;
     a.K = p.K;
     a.Rf = p.Rf;
+    a.rfm = static_cast<uint32_t>(((uint64_t(1) << 32) + p.Rf - 1) / p.Rf);
     a.ar = p.ar;
     a.pixgroup = p.pixgroup;
     a.maxb = p.R - f->L;
@@ -824,21 +946,21 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
         a.tile0 = t0;
         a.wave_tiles = static_cast<int>(std::min<long long>(p.wave_tiles, p.ntiles - t0));
         if (a.tilemax) MORPH_CUDA_TRY(cudaMemsetAsync(a.tilemax, 0xff, sizeof(int) * a.wave_tiles, st));
-        const size_t sr = smem_rows(p.ax.N, prec) + 4 * static_cast<size_t>(p.Win_x);
         prof_begin(ctx, st, prec == 4 ? "k_fft_rows_fwd<f32>" : "k_fft_rows_fwd<f64>");
-        k_fft_rows_fwd<T><<<dim3(p.Rin_y, a.wave_tiles), 256, sr, st>>>(a);
+        rows_fwd_for<T>(p.kgroup)<<<dim3(p.Rin_y, a.wave_tiles), 256, smem_rows(p.ax.N, p.kgroup, prec), st>>>(a);
         prof_end(ctx, st);
         prof_begin(ctx, st, prec == 4 ? "k_fft_cols<f32>" : "k_fft_cols<f64>");
-        k_fft_cols<T><<<dim3((p.ax.N + p.colgroup - 1) / p.colgroup, p.K, a.wave_tiles), 256,
-                         smem_cols(p.ay.N, p.colgroup, prec), st>>>(a);
+        cols_for<T>(p.colgroup)<<<dim3(a.wave_tiles, (p.ax.N + p.colgroup - 1) / p.colgroup, p.K), p.col_threads,
+                                  smem_cols(p.ay.N, p.colgroup, prec), st>>>(a);
         prof_end(ctx, st);
         prof_begin(ctx, st, prec == 4 ? "k_fft_rows_inv<f32>" : "k_fft_rows_inv<f64>");
-        k_fft_rows_inv<T><<<dim3(p.To_y, p.K, a.wave_tiles), 256, smem_rows(p.ax.N, prec), st>>>(a);
+        rows_inv_for<T>(p.kgroup)<<<dim3(p.To_y, (p.K + p.kgroup - 1) / p.kgroup, a.wave_tiles), 256,
+                                    smem_rows(p.ax.N, p.kgroup, prec), st>>>(a);
         prof_end(ctx, st);
         if (p.range_fft) {
-            const size_t srange = static_cast<size_t>(p.Rf) * (1 + 2 * p.pixgroup) * 2 * prec;
             prof_begin(ctx, st, prec == 4 ? "k_fft_range<f32>" : "k_fft_range<f64>");
-            k_fft_range<T><<<dim3((p.To_x + p.pixgroup - 1) / p.pixgroup, p.To_y, a.wave_tiles), 256, srange, st>>>(a);
+            range_for<T>(p.pixgroup)<<<dim3((p.To_x + p.pixgroup - 1) / p.pixgroup, p.To_y, a.wave_tiles),
+                                       p.pix_threads, smem_cols(p.Rf, p.pixgroup, prec), st>>>(a);
             prof_end(ctx, st);
         } else {
             const long long px = static_cast<long long>(p.To_y) * p.To_x * a.wave_tiles;

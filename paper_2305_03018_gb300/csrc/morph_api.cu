@@ -261,7 +261,7 @@ size_t planes_bytes(const morph_image* f) {
 // L = 16 / 64 / 256, SEs 3^2..256^2; median error about 10 %):
 //   direct: 54 us + 1.07 x issued FLOP / 3e15 + 12.2 ns per tile pass
 //           (epilogue) + 0.76 ps per pixel level (encoder);
-//   FFT32 : 79 us + FFT FLOP / 2.16e12;  FFT64: 145 us + FFT FLOP / 6.9e11;
+//   FFT32 : 70 us + FFT FLOP / 5.55e12;  FFT64: 92 us + FFT FLOP / 7.25e11;
 //   NTT   : 80 us + 1.48 x its own estimate (operations, bytes, CTAs).
 static double direct_time(const DirectPlan& dp, const morph_image* f) {
     return 54e-6 + 1.07 * dp.issued_flop / 3.0e15 + 12.2e-9 * static_cast<double>(dp.tiles) * dp.T * dp.n_pass +
@@ -291,7 +291,7 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
         FftPlan fp;
         const bool f32_ok = plan_fft_tiles(f, se, 4, false, &fp) == MORPH_OK;
         if (f32_ok) {
-            const double t = 79e-6 + fp.flop / 2.16e12;
+            const double t = 70e-6 + fp.flop / 5.55e12;
             if (t < best) { best = t; *route = ROUTE_FFT32; }
         }
         NttPlan np;
@@ -301,7 +301,7 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
         } else if (!f32_ok) {
             FftPlan f64;
             if (plan_fft_tiles(f, se, 8, false, &f64) == MORPH_OK) {
-                const double t = 145e-6 + f64.flop / 6.9e11;
+                const double t = 92e-6 + f64.flop / 7.25e11;
                 if (t < best) { best = t; *route = ROUTE_FFT64; }
             }
         }
@@ -356,13 +356,13 @@ int tune_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int er
     cand.push_back({ROUTE_DIRECT, direct_time(dp, f)});
     FftPlan fp;
     const bool f32_ok = plan_fft_tiles(f, &e.se, 4, false, &fp) == MORPH_OK;
-    if (f32_ok) cand.push_back({ROUTE_FFT32, 79e-6 + fp.flop / 2.16e12});
+    if (f32_ok) cand.push_back({ROUTE_FFT32, 70e-6 + fp.flop / 5.55e12});
     NttPlan np;
     const bool ntt_ok = plan_ntt_tiles(f, &e.se, &np) == MORPH_OK;
     if (ntt_ok) cand.push_back({ROUTE_NTT, 80e-6 + 1.2 * ntt_time_estimate(np)});
     if (!f32_ok && !ntt_ok) {
         FftPlan f64;
-        if (plan_fft_tiles(f, &e.se, 8, false, &f64) == MORPH_OK) cand.push_back({ROUTE_FFT64, 145e-6 + f64.flop / 6.9e11});
+        if (plan_fft_tiles(f, &e.se, 8, false, &f64) == MORPH_OK) cand.push_back({ROUTE_FFT64, 92e-6 + f64.flop / 7.25e11});
     }
     double best_est = 1e30;
     for (const auto& c : cand) best_est = std::min(best_est, c.second);

@@ -139,7 +139,7 @@ int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts*
     for (int i : b->fft_items) {
         const Plan& pl = *b->items[i].plan;
         const double c = pl.route == ROUTE_NTT ? ntt_time_estimate(pl.ntt)
-                                               : pl.fft.flop / (pl.fft.prec == 4 ? 2.16e12 : 6.9e11);
+                                               : pl.fft.flop / (pl.fft.prec == 4 ? 5.55e12 : 7.25e11);
         cost.push_back({c, i});
     }
     std::stable_sort(cost.begin(), cost.end(), [](const auto& x, const auto& y) { return x.first > y.first; });

@@ -93,6 +93,8 @@ struct FftAxis {
     int N;         // transform length (2^a 3^b 5^c, <= 2048)
     int nst;       // Stockham stages
     int rad[16];   // radix of each stage (4, 2, 3, 5)
+    int tstep[16];       // N / (Ns R): twiddle stride of each stage
+    uint32_t nsm[16];    // ceil(2^32 / Ns), Ns the product of the earlier radices (0 for Ns = 1)
 };
 
 struct FftPlan {
@@ -104,6 +106,8 @@ struct FftPlan {
     int tiles_y = 0, tiles_x = 0;
     long long ntiles = 0;
     int wave_tiles = 0, colgroup = 4, pixgroup = 16;
+    int kgroup = 1;               // grey frequencies per pass of the row kernels (power of two)
+    int col_threads = 256, pix_threads = 256;
     size_t buf_bytes = 0;         // spectra of one wave of tiles
     size_t ws_bytes = 0;          // buf_bytes + per-tile scan bounds
     bool range_fft = false;       // grey-axis inverse by FFT (long axes) or by direct evaluation
