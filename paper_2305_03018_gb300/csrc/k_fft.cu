@@ -228,7 +228,7 @@ __device__ __forceinline__ void tile_origin(const FftArgs& a, long long gt, int*
 // grid (Rin_y, wave_tiles): input row rho of tile tl; the K grey frequencies
 // B at a time (B interleaved row transforms per pass)
 template <typename T, int B>
-__global__ void __launch_bounds__(256) k_fft_rows_fwd(const FftArgs a) {
+__global__ void __launch_bounds__(512) k_fft_rows_fwd(const FftArgs a) {
     using cT = typename CxT<T>::type;
     constexpr int PB = fpitch(B);
     extern __shared__ __align__(16) unsigned char sm[];
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(512) k_fft_cols(const FftArgs a) {
 // grid (To_y, ceil(K / B), wave_tiles): inverse row FFT of output row q for B
 // grey frequencies, keep the output columns
 template <typename T, int B>
-__global__ void __launch_bounds__(256) k_fft_rows_inv(const FftArgs a) {
+__global__ void __launch_bounds__(512) k_fft_rows_inv(const FftArgs a) {
     using cT = typename CxT<T>::type;
     constexpr int PB = fpitch(B);
     extern __shared__ __align__(16) unsigned char sm[];
@@ -734,8 +734,9 @@ int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unpr
     while (p->colgroup > 1 && smem_cols(p->ay.N, p->colgroup, prec) > kFftSmemQuarter) p->colgroup /= 2;
     p->pixgroup = 32;
     while (p->pixgroup > 1 && smem_cols(p->Rf, p->pixgroup, prec) > kFftSmemHalf) p->pixgroup /= 2;
-    p->col_threads = p->ay.N * p->colgroup >= 8192 ? 512 : 256;
-    p->pix_threads = p->Rf * p->pixgroup >= 8192 ? 512 : 256;
+    p->col_threads = p->ay.N * p->colgroup >= 2048 ? 512 : 256;
+    p->pix_threads = p->Rf * p->pixgroup >= 4096 ? 512 : 256;
+    p->row_threads = p->ax.N * p->kgroup >= 2048 ? 512 : 256;
     const size_t per_tile = static_cast<size_t>(p->K) * p->ax.N * p->ay.N * 2 * prec;
     const size_t budget = size_t(4) << 30;
     long long wt = static_cast<long long>(budget / std::max<size_t>(per_tile, 1));
@@ -947,14 +948,15 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
         a.wave_tiles = static_cast<int>(std::min<long long>(p.wave_tiles, p.ntiles - t0));
         if (a.tilemax) MORPH_CUDA_TRY(cudaMemsetAsync(a.tilemax, 0xff, sizeof(int) * a.wave_tiles, st));
         prof_begin(ctx, st, prec == 4 ? "k_fft_rows_fwd<f32>" : "k_fft_rows_fwd<f64>");
-        rows_fwd_for<T>(p.kgroup)<<<dim3(p.Rin_y, a.wave_tiles), 256, smem_rows(p.ax.N, p.kgroup, prec), st>>>(a);
+        rows_fwd_for<T>(p.kgroup)<<<dim3(p.Rin_y, a.wave_tiles), p.row_threads, smem_rows(p.ax.N, p.kgroup, prec),
+                                    st>>>(a);
         prof_end(ctx, st);
         prof_begin(ctx, st, prec == 4 ? "k_fft_cols<f32>" : "k_fft_cols<f64>");
         cols_for<T>(p.colgroup)<<<dim3(a.wave_tiles, (p.ax.N + p.colgroup - 1) / p.colgroup, p.K), p.col_threads,
                                   smem_cols(p.ay.N, p.colgroup, prec), st>>>(a);
         prof_end(ctx, st);
         prof_begin(ctx, st, prec == 4 ? "k_fft_rows_inv<f32>" : "k_fft_rows_inv<f64>");
-        rows_inv_for<T>(p.kgroup)<<<dim3(p.To_y, (p.K + p.kgroup - 1) / p.kgroup, a.wave_tiles), 256,
+        rows_inv_for<T>(p.kgroup)<<<dim3(p.To_y, (p.K + p.kgroup - 1) / p.kgroup, a.wave_tiles), p.row_threads,
                                     smem_rows(p.ax.N, p.kgroup, prec), st>>>(a);
         prof_end(ctx, st);
         if (p.range_fft) {

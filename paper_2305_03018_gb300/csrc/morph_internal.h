@@ -107,7 +107,7 @@ struct FftPlan {
     long long ntiles = 0;
     int wave_tiles = 0, colgroup = 4, pixgroup = 16;
     int kgroup = 1;               // grey frequencies per pass of the row kernels (power of two)
-    int col_threads = 256, pix_threads = 256;
+    int col_threads = 256, pix_threads = 256, row_threads = 256;
     size_t buf_bytes = 0;         // spectra of one wave of tiles
     size_t ws_bytes = 0;          // buf_bytes + per-tile scan bounds
     bool range_fft = false;       // grey-axis inverse by FFT (long axes) or by direct evaluation
