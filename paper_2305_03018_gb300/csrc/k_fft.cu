@@ -18,17 +18,19 @@
 // the nearest integer and takes the highest d with C >= 1.
 //
 // Kernels (per wave of tiles):
-//   k_fft_rows_fwd : encode a_k for one input row, FFT along x, for every k;
+//   k_fft_rows_fwd : encode a_k for one input row, FFT along x, a batch of k
+//                    per pass;
 //   k_fft_cols     : FFT along y of C columns, multiply by the SE spectrum,
 //                    inverse FFT along y, keep the output rows;
-//   k_fft_rows_inv : inverse FFT along x of one output row, keep the output columns;
+//   k_fft_rows_inv : inverse FFT along x of one output row for a batch of k,
+//                    keep the output columns;
 //   k_fft_scan     : grey-axis inverse by direct evaluation, downward from a
 //                    proven start degree, stopping at the top (short grey axes);
 //   k_fft_range    : grey-axis inverse FFT of a group of pixels + rounding +
 //                    top-degree scan (one warp per pixel, ballots over d).
 // The FFTs are mixed-radix (2, 3, 4, 5) Stockham transforms in shared memory
-// with twiddle tables computed in FP64 (sincospi) and rounded to the working
-// precision.
+// over power-of-two batches of interleaved transforms, with twiddle tables
+// computed in FP64 (sincospi) and rounded to the working precision.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -205,8 +207,6 @@ struct FftArgs {
     float* count_err;
     int validate;
     unsigned int* err;
-    int colgroup;             // columns per CTA in k_fft_cols
-    int pixgroup;             // pixels per CTA in k_fft_range
     int* tilemax;             // [wave_tiles] largest grey level in each input tile (k_fft_scan start bound)
     int maxb;                 // largest SE offset
 };
@@ -918,7 +918,6 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
     a.Rf = p.Rf;
     a.rfm = static_cast<uint32_t>(((uint64_t(1) << 32) + p.Rf - 1) / p.Rf);
     a.ar = p.ar;
-    a.pixgroup = p.pixgroup;
     a.maxb = p.R - f->L;
     a.tilemax = p.range_fft ? nullptr : reinterpret_cast<int*>(static_cast<unsigned char*>(buf) + p.buf_bytes);
     a.To_y = p.To_y;
@@ -941,7 +940,6 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
     a.count_err = count_err;
     a.validate = validate;
     a.err = ctx->d_err;
-    a.colgroup = p.colgroup;
     const int prec = static_cast<int>(sizeof(T));
     for (long long t0 = 0; t0 < p.ntiles; t0 += p.wave_tiles) {
         a.tile0 = t0;
