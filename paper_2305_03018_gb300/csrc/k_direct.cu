@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
             const TileCoord tc = direct_tile(P, t);
             const int* rb = P->meta;
             const int* rows = P->meta + (P->n_pass + 1) + P->n_pass * 8;
-            const int xw = tc.j0 - (P->kw - 1) + P->ox;   // first image column of the K window (16-aligned)
+            const int xw = tc.j0 - (P->kw - 1) + P->ox + P->shift;   // plane column of the K window (32-aligned)
             for (int p = 0; ok && p < P->n_pass; ++p) {
                 for (int q = rb[p]; ok && q < rb[p + 1]; ++q) {
                     const int r = rows[q];
@@ -400,7 +400,9 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     p->h = f->h;
     p->w = f->w;
     p->nimg = f->n;
-    p->w_pad = (f->w + 15) & ~15;
+    // plane pitch: a multiple of 32 bytes with room for any shift 0..31 (the planes' size
+    // depends on the image only)
+    p->w_pad = (f->w + 31 + 31) & ~31;
     // distinct offset levels among the taps
     std::vector<int> levels;
     int taps = 0, maxb = 0;
@@ -438,9 +440,12 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     // two tiles per unit when both windows fit one 128-byte stage and the image is wide enough
     // (the second tile's K-steps read up to J + 32 ksteps bytes into the 128-byte rows)
     p->T = (2 * p->J + kw - 1 <= 128 && p->J + 32 * p->ksteps <= 128 && f->w > p->J) ? 2 : 1;
-    const int a = (((kw - 1 - se->ox) % 16) + 16) % 16;
-    p->e = (16 - a) % 16;
-    p->tiles_x = (f->w + p->e + p->T * p->J - 1) / (p->T * p->J);
+    // K windows start at image column j0 - (kw - 1 - ox): shifting the planes by that amount mod 32
+    // puts every window of a tile grid starting at column 0 on a 32-byte boundary (TMA needs 16;
+    // 32 keeps each 128-byte box row on four whole L2 sectors)
+    p->shift = (((kw - 1 - se->ox) % 32) + 32) % 32;
+    p->e = 0;
+    p->tiles_x = (f->w + p->T * p->J - 1) / (p->T * p->J);
     p->tiles_y = (f->h + p->rows_n - 1) / p->rows_n;
     p->tiles = static_cast<long long>(f->n) * p->tiles_x * p->tiles_y;
     // meta: pass_row_begin[n_pass + 1], group_w[n_pass * 8], rows[]
@@ -520,7 +525,7 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
                          int32_t* out_cnt, long long tile_base, int* status) {
     std::memset(static_cast<void*>(d), 0, sizeof(*d));
     d->tmA = p.tmA;
-    const uint64_t dims[4] = {static_cast<uint64_t>(p.w), static_cast<uint64_t>(p.L), static_cast<uint64_t>(p.h),
+    const uint64_t dims[4] = {static_cast<uint64_t>(p.w + p.shift), static_cast<uint64_t>(p.L), static_cast<uint64_t>(p.h),
                               static_cast<uint64_t>(p.nimg)};
     const uint64_t strides[3] = {static_cast<uint64_t>(p.w_pad), static_cast<uint64_t>(p.w_pad) * p.L,
                                  static_cast<uint64_t>(p.w_pad) * p.L * p.h};
@@ -545,6 +550,7 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
     d->oy = p.oy;
     d->ox = p.ox;
     d->e = p.e;
+    d->shift = p.shift;
     d->erode = p.erode;
     d->T = p.T;
     d->tiles_x = p.tiles_x;

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_encode_planes(const EncodeJob* __restri
         const long long row = local / cb_per_row;           // n * h + i
         const int i = static_cast<int>(row % J->h);
         const int n = static_cast<int>(row / J->h);
-        const int j0 = cb << 4;
+        const int j0 = cb << 4;                              // plane column of the first byte
         // levels of the 16 pixels; `valid` has 0xFF in the bytes of present, in-range pixels
         uint32_t packed[4] = {0u, 0u, 0u, 0u};
         uint32_t valid[4] = {0u, 0u, 0u, 0u};
@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(256) k_encode_planes(const EncodeJob* __restri
         bool bad = false;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const int j = j0 + k;
-            if (j < J->w) {
+            const int j = j0 + k - J->shift;                  // image column
+            if (j >= 0 && j < J->w) {
                 int val = load_pixel(J->src, J->dtype, base + j);
                 if (val < 0 || val >= J->L) {
                     bad = true;

@@ -248,7 +248,7 @@ static int get_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, in
 }
 
 size_t planes_bytes(const morph_image* f) {
-    const size_t w_pad = (static_cast<size_t>(f->w) + 15) & ~size_t(15);
+    const size_t w_pad = (static_cast<size_t>(f->w) + 62) & ~size_t(31);   // the direct plan's pitch
     return static_cast<size_t>(f->n) * f->h * f->L * w_pad;
 }
 
@@ -447,6 +447,7 @@ static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int er
     job.flip = erode;
     job.planes = planes;
     job.w_pad = dp.w_pad;
+    job.shift = dp.shift;
     job.item_base = 0;
     const long long items = static_cast<long long>(f->n) * f->h * (dp.w_pad / 16);
     rc = launch_encode(ctx, &job, 1, items, nullptr, st);

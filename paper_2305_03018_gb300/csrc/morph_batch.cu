@@ -180,6 +180,7 @@ int batch_descriptors(morph_batch* b, uint8_t* ws) {
         job.flip = it.erode;
         job.planes = ws + it.planes_off;
         job.w_pad = dp.w_pad;
+        job.shift = dp.shift;
         job.item_base = b->enc_items;
         b->enc_items += static_cast<long long>(it.f.n) * it.f.h * (dp.w_pad / 16);
         b->jobs.push_back(job);

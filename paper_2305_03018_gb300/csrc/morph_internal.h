@@ -27,9 +27,11 @@ void set_last_cuda_error(cudaError_t e, const char* expr, const char* file, int 
 
 // --------------------------------------------------- encoder (Step 1, Eq. 7)
 // One image batch is written as FP8 E4M3 indicator planes
-//   planes[n][i][v][j] = 1.0 if level(f(n,i,j)) == v else 0,  j < W,
+//   planes[n][i][v][c] = 1.0 if level(f(n,i,c - shift)) == v else 0,
 // with level(f) = f (dilation) or L-1-f (erosion by duality); row pitch
-// w_pad (a multiple of 16 bytes), columns w..w_pad-1 zero.
+// w_pad (a multiple of 16 bytes), columns outside [shift, shift + w) zero.
+// The shift (0..31) puts the K windows of the direct route's tiles on
+// 32-byte boundaries without shifting the tile grid.
 struct EncodeJob {
     const void* src;
     int dtype;              // morph_dtype
@@ -39,6 +41,7 @@ struct EncodeJob {
     int flip;               // 1: level = L-1-f
     uint8_t* planes;
     int w_pad;
+    int shift;              // plane column of image column 0
     long long item_base;    // first work item of this job (batched launch)
 };
 
@@ -57,6 +60,7 @@ struct DirectProblemDev {
     int Lpad, rows_n, J, G;
     int n_pass, nk, ksteps, kw;
     int oy, ox, e, erode;
+    int shift;              // plane column of image column 0 (TMA x = image column + shift)
     int T;                  // horizontally adjacent tiles sharing each A/B stage (1 or 2)
     int tiles_x, tiles_y;   // units (of T tiles) across, tile rows down
     long long tile_base;    // first global tile of this problem
@@ -73,7 +77,7 @@ struct DirectLaunch {
 
 struct DirectPlan {
     int L = 0, Lpad = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0, T = 1;
-    int kh = 0, kw = 0, oy = 0, ox = 0, e = 0, erode = 0;
+    int kh = 0, kw = 0, oy = 0, ox = 0, e = 0, erode = 0, shift = 0;
     int h = 0, w = 0, nimg = 0, w_pad = 0;
     int tiles_x = 0, tiles_y = 0;
     long long tiles = 0;

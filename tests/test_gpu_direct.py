@@ -173,7 +173,7 @@ def test_workspace_size_matches_plan_and_is_host_only():
         for op in (0, 1):
             ws = ctx.workspace_size(f, 64, se, op=op, method=method)
             assert ws == ctx.plan(f, 64, se, op=op, method=method).workspace_bytes, (method, op)
-    assert ctx.workspace_size(f, 64, se, op=0, method="direct_fp8") == 2 * 200 * 64 * 304
+    assert ctx.workspace_size(f, 64, se, op=0, method="direct_fp8") == 2 * 200 * 64 * 352
     # backward: one float share per pixel (rounded to 256 B) plus one partial sum per (tap, chunk)
     ntaps = int(np.count_nonzero(se.mask))
     chunks = 2 * ((200 + (8192 // 300) - 1) // (8192 // 300))

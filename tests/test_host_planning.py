@@ -34,8 +34,8 @@ def test_direct_and_backward_sizes_follow_their_layouts():
     g = wl.rng(61)
     se = wl.se_random(g, 9, 7, 0.6, 5)
     im = _img(2, 200, 300, 64)
-    # indicator planes: n h L round16(w) bytes
-    assert _ws(im, se, 0, "direct_fp8") == _ws(im, se, 1, "direct_fp8") == 2 * 200 * 64 * 304
+    # indicator planes: n h L round32(w + 31) bytes (room for the column shift that aligns K windows)
+    assert _ws(im, se, 0, "direct_fp8") == _ws(im, se, 1, "direct_fp8") == 2 * 200 * 64 * 352
     # backward: a float share per pixel (256-byte rounded) + a partial sum per (tap, chunk of <= 8192 px)
     ntaps = int(np.count_nonzero(se.mask))
     rows_per_chunk = 8192 // 300
@@ -89,7 +89,7 @@ def test_huge_offsets_plan_only_the_fp8_route():
     o = np.array([[0, 65535, 7], [3, 0, 40000], [1, 2, 3]], np.int32)
     se = wl.SE(m, o, (1, 1), "huge")
     im = _img(1, 64, 64, 256)
-    assert _ws(im, se, 0, "auto") == _ws(im, se, 0, "direct_fp8") == 64 * 256 * 64
+    assert _ws(im, se, 0, "auto") == _ws(im, se, 0, "direct_fp8") == 64 * 256 * 96   # planes: h L round32(w + 31)
     for method in ("ntt", "fft_f64"):
         with pytest.raises(M.MorphError) as ei:
             _ws(im, se, 0, method)
