@@ -183,6 +183,10 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
     } else if (warp == 1 && lane == 0) {
         // -------------------------------------------------------- MMA issuer
         const uint32_t idesc = idesc_e4m3_f32(kDirectM, kDirectN);
+        // the issuing thread is on the critical path: stage barriers and descriptors are stepped
+        // from slot 0's by plain additions, loop bounds are read once per pass
+        const uint32_t full0 = smem_u32(&tail->full[0]), empty0 = smem_u32(&tail->empty[0]);
+        const uint64_t desc0 = umma_desc_sw128(smem_u32(base));
         uint32_t it = 0;
         uint32_t use0 = 0u, use1 = 0u;   // completed claims of TMEM accumulator slots 0 and 1
         uint32_t next_slot = 0;
@@ -205,15 +209,15 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + s0 * kDirectN;
                 uint32_t acc = 0;
-                for (int q = rb[p]; ok && q < rb[p + 1]; ++q) {
+                const int q_end = rb[p + 1];
+                for (int q = rb[p]; ok && q < q_end; ++q) {
                     for (int kc = 0; kc < nk; ++kc) {
-                        const int s = static_cast<int>(it % kStages);
+                        const uint32_t s = it % kStages;
                         const uint32_t ph = (it / kStages) & 1u;
-                        if (!mbar_wait(smem_u32(&tail->full[s]), ph, abort_flag, dl.err)) { ok = false; break; }
+                        if (!mbar_wait(full0 + 8u * s, ph, abort_flag, dl.err)) { ok = false; break; }
                         tc_fence_after();
-                        const uint8_t* sa = base + s * kStageBytes;
-                        const uint64_t adesc = umma_desc_sw128(smem_u32(sa));
-                        const uint64_t bdesc = umma_desc_sw128(smem_u32(sa + kStageA));
+                        const uint64_t adesc = desc0 + static_cast<uint64_t>(s * (kStageBytes >> 4));
+                        const uint64_t bdesc = adesc + static_cast<uint64_t>(kStageA >> 4);
                         const int nks = min(4, ksteps - 4 * kc);
                         // advance the start addresses by 32 B of K inside the 128-B swizzled rows
                         if (two) {
@@ -229,7 +233,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                                 acc = 1;
                             }
                         }
-                        tc_commit(smem_u32(&tail->empty[s]));
+                        tc_commit(empty0 + 8u * s);
                         ++it;
                     }
                 }
