@@ -143,6 +143,8 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------------ TMA producer
+        const uint32_t full0 = smem_u32(&tail->full[0]), empty0 = smem_u32(&tail->empty[0]);
+        const uint32_t ring0 = smem_u32(base);
         uint32_t it = 0;
         bool ok = true;
         for (long long t = blockIdx.x; ok && t < dl.total_tiles; t += gridDim.x) {
@@ -155,18 +157,20 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
             const int* rb = P->meta;
             const int* rows = P->meta + (P->n_pass + 1) + P->n_pass * 8;
             const int xw = tc.j0 - (P->kw - 1) + P->ox + P->shift;   // plane column of the K window (32-aligned)
-            for (int p = 0; ok && p < P->n_pass; ++p) {
-                for (int q = rb[p]; ok && q < rb[p + 1]; ++q) {
-                    const int r = rows[q];
-                    for (int kc = 0; kc < P->nk; ++kc) {
-                        const int s = static_cast<int>(it % kStages);
+            const int y0 = tc.i0 + P->oy, nk = P->nk, n_pass = P->n_pass;
+            for (int p = 0; ok && p < n_pass; ++p) {
+                const int q_end = rb[p + 1];
+                for (int q = rb[p]; ok && q < q_end; ++q) {
+                    const int y = y0 - rows[q];
+                    for (int kc = 0; kc < nk; ++kc) {
+                        const uint32_t s = it % kStages;
                         const uint32_t ph = (it / kStages) & 1u;
-                        if (!mbar_wait(smem_u32(&tail->empty[s]), ph ^ 1u, abort_flag, dl.err)) { ok = false; break; }
-                        const uint32_t fb = smem_u32(&tail->full[s]);
+                        if (!mbar_wait(empty0 + 8u * s, ph ^ 1u, abort_flag, dl.err)) { ok = false; break; }
+                        const uint32_t fb = full0 + 8u * s;
                         mbar_arrive_expect_tx(fb, kStageBytes);
-                        uint8_t* sa = base + s * kStageBytes;
-                        tma_load_2d(smem_u32(sa), &P->tmA, 0, (q * P->nk + kc) * 128, fb);
-                        tma_load_4d(smem_u32(sa + kStageA), &P->tmB, xw + 128 * kc, 0, tc.i0 - r + P->oy, tc.n, fb);
+                        const uint32_t sa = ring0 + s * kStageBytes;
+                        tma_load_2d(sa, &P->tmA, 0, (q * nk + kc) * 128, fb);
+                        tma_load_4d(sa + kStageA, &P->tmB, xw + 128 * kc, 0, y, tc.n, fb);
                         ++it;
                     }
                 }
@@ -273,7 +277,41 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 if (epi_any_failed(!ok)) { failed = true; break; }
                 tc_fence_after();
                 const int wg = (g < G) ? gw[p * 8 + g] : 0;
+                // (max, sum-at-max) over the groups of tile tt, merged with the earlier passes
+                const int pairs = rows_n * J;
+                auto reduce = [&](int tt, int rbase) {
+                    for (int idx = et; idx < pairs; idx += 128) {
+                        const int tr = idx / J, jl = idx - tr * J;
+                        int best = -1, bc = 0;
+                        for (int gg = 0; gg < G; ++gg) {
+                            const int2 e = red[rbase + tr * 128 + gg * J + jl];
+                            if (e.x > best) { best = e.x; bc = e.y; }
+                            else if (e.x == best && e.x >= 0) bc += e.y;
+                        }
+                        int2 cur = make_int2(best, bc);
+                        const int ri = tt * pairs + idx;
+                        if (p > 0) {
+                            const int2 prev = run[ri];
+                            if (prev.x > cur.x) cur = prev;
+                            else if (prev.x == cur.x && cur.x >= 0) cur.y += prev.y;
+                        }
+                        run[ri] = cur;
+                        if (p == P->n_pass - 1) {
+                            const int i = tc.i0 + tr, j = tc.j0 + tt * J + jl;
+                            if (i < P->h && j >= 0 && j < P->w) {
+                                const int dval = cur.x < 0 ? 0 : cur.x;
+                                const long long o = (static_cast<long long>(tc.n) * P->h + i) * P->w + j;
+                                P->out[o] = P->erode ? (P->L - 1 - dval) : dval;
+                                if (P->out_cnt) P->out_cnt[o] = cur.x < 0 ? 0 : cur.y;
+                            }
+                        }
+                    }
+                };
+                // with two tiles whose lane results both fit `red`, read both accumulators and hand
+                // them back before reducing, so the next unit's MMAs wait only for the TMEM reads
+                const bool reads_first = T == 2 && 2 * rows_n * 128 <= kRedEntries;
                 for (int tt = 0; tt < T; ++tt) {
+                    const int rbase = reads_first ? tt * rows_n * 128 : 0;
                     const uint32_t trow =
                         tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + (s0 + tt) * kDirectN;
                     for (int tr = 0; tr < rows_n; ++tr) {
@@ -300,41 +338,23 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                                 }
                             }
                         }
-                        red[tr * 128 + m] =
+                        red[rbase + tr * 128 + m] =
                             (top >= 0) ? make_int2(top + wg, __float2int_rn(cnt)) : make_int2(-1, 0);
                     }
                     // this accumulator's TMEM reads are done: hand it back
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&tail->tempty[s0 + tt]));
-                    epi_bar();
-                    const int pairs = rows_n * J;
-                    for (int idx = et; idx < pairs; idx += 128) {
-                        const int tr = idx / J, jl = idx - tr * J;
-                        int best = -1, bc = 0;
-                        for (int gg = 0; gg < G; ++gg) {
-                            const int2 e = red[tr * 128 + gg * J + jl];
-                            if (e.x > best) { best = e.x; bc = e.y; }
-                            else if (e.x == best && e.x >= 0) bc += e.y;
-                        }
-                        int2 cur = make_int2(best, bc);
-                        const int ri = tt * pairs + idx;
-                        if (p > 0) {
-                            const int2 prev = run[ri];
-                            if (prev.x > cur.x) cur = prev;
-                            else if (prev.x == cur.x && cur.x >= 0) cur.y += prev.y;
-                        }
-                        run[ri] = cur;
-                        if (p == P->n_pass - 1) {
-                            const int i = tc.i0 + tr, j = tc.j0 + tt * J + jl;
-                            if (i < P->h && j >= 0 && j < P->w) {
-                                const int dval = cur.x < 0 ? 0 : cur.x;
-                                const long long o = (static_cast<long long>(tc.n) * P->h + i) * P->w + j;
-                                P->out[o] = P->erode ? (P->L - 1 - dval) : dval;
-                                if (P->out_cnt) P->out_cnt[o] = cur.x < 0 ? 0 : cur.y;
-                            }
-                        }
+                    if (!reads_first) {
+                        epi_bar();
+                        reduce(tt, 0);
+                        epi_bar();
                     }
+                }
+                if (reads_first) {
+                    epi_bar();
+                    reduce(0, 0);
+                    reduce(1, rows_n * 128);
                     epi_bar();
                 }
                 if (T == 2 || s0 == 0u) ++use0;
