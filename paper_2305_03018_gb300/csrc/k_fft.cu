@@ -543,10 +543,12 @@ __global__ void __launch_bounds__(256) k_plane_rows(double2* planes, FftAxis ax,
     for (int j = threadIdx.x; j < Nx; j += blockDim.x) p[j] = res[j];
 }
 
-constexpr int kPlaneCols = 4;   // columns per CTA of k_plane_cols
+constexpr int kPlaneCols = 4;   // columns per CTA of k_plane_cols, where they fit shared memory
+constexpr int kPlaneSmem = 200 * 1024;   // dynamic shared memory opted into by the plane kernels
 
+template <int C>
 __global__ void __launch_bounds__(256) k_plane_cols(double2* planes, FftAxis ay, const double2* gtw, int Nx) {
-    constexpr int C = kPlaneCols, PC = fpitch(C);
+    constexpr int PC = fpitch(C);
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = ay.N;
     double2* tw = reinterpret_cast<double2*>(sm);
@@ -816,9 +818,10 @@ static int set_fft_smem() {
 static int set_plane_smem() {
     static bool done = false;
     if (done) return MORPH_OK;
-    const int big = 200 * 1024;
+    const int big = kPlaneSmem;
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_plane_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_plane_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_plane_cols<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    MORPH_CUDA_TRY(cudaFuncSetAttribute(k_plane_cols<kPlaneCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     done = true;
     return MORPH_OK;
 }
@@ -875,8 +878,12 @@ int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int
         k_se_scatter<<<blocks, 256>>>(s64, K, Ny, Nx, d_taps, static_cast<int>(taps.size()), Rf);
     }
     k_plane_rows<<<dim3(Ny, K), 256, smem_rows(Nx, 1, 8)>>>(s64, p->ax, tw64x, Ny);
-    k_plane_cols<<<dim3((Nx + kPlaneCols - 1) / kPlaneCols, K), 256, smem_cols(Ny, kPlaneCols, 8)>>>(s64, p->ay,
-                                                                                                     tw64y, Nx);
+    // four columns per CTA up to Ny = 1024 (180 KB); one at Ny = 2048 (four would need 360 KB)
+    if (smem_cols(Ny, kPlaneCols, 8) <= static_cast<size_t>(kPlaneSmem))
+        k_plane_cols<kPlaneCols><<<dim3((Nx + kPlaneCols - 1) / kPlaneCols, K), 256, smem_cols(Ny, kPlaneCols, 8)>>>(
+            s64, p->ay, tw64y, Nx);
+    else
+        k_plane_cols<1><<<dim3(Nx, K), 256, smem_cols(Ny, 1, 8)>>>(s64, p->ay, tw64y, Nx);
     ctx->launches += 5;
     MORPH_CUDA_TRY(cudaGetLastError());
     if (prec == 4) {

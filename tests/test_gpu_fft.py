@@ -131,3 +131,15 @@ def test_origin_outside_the_box(ctx, method, origin):
     se = wl.se_random(g, 6, 4, 0.6, 4, origin=origin, force_origin=False)
     for op in ("dilate", "erode"):
         _eq(_run(ctx, f, 32, se, op, method), _ref(f, 32, se, op))
+
+
+def test_fp64_long_column_axis(ctx):
+    # a 2048^2 image with a 204^2 full filter plans column transforms longer than 1163 points:
+    # the SE spectrum's column pass then no longer fits four columns per CTA in shared memory
+    g = wl.rng(2048 + 204 + 4)
+    f = g.integers(0, 16, size=(1, 2048, 2048)).astype(np.uint8)
+    se = wl.se_full_random(g, 204, 15)
+    info = ctx.plan(torch.from_numpy(f).cuda(), 16, se, method="fft_f64")
+    assert info.fft_ny * 16 * 11 > 200 * 1024, info.fft_ny
+    rows = (1000, 1002)
+    _eq(_run(ctx, f, 16, se, "dilate", "fft_f64"), _ref(f, 16, se, "dilate", rows=rows), rows=rows)
