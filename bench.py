@@ -680,7 +680,8 @@ def run_sweep(args, ws, rank, local):
                          "s_per_op": {m: (r["ms_per_step"] * 1e-3 if r.get("ms_per_step") else None)
                                       for m, r in res.items()},
                          "exact_vs_first": all(r.get("exact_vs_first", False) for r in res.values()
-                                               if "note" not in r)})
+                                               if "note" not in r),
+                         "notes": {m: r["note"] for m, r in res.items() if "note" in r}})
             del f
             torch.cuda.empty_cache()
     line = {"metric": METRIC, "workload": args.workload, "unit": "s per dilation", "steps": max(1, args.steps),
