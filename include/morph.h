@@ -118,6 +118,9 @@ typedef struct {
     int tile_w, tile_h;      /* direct route: output tile (columns x rows) */
     double est_flop;         /* issued dense FLOP (direct) or FFT FLOP (FFT routes) */
     size_t workspace_bytes;  /* device workspace the call needs */
+    int unit_tiles;          /* direct route: horizontally adjacent tiles per work unit (1 or 2) */
+    int unit_blocks;         /* direct route: 128-byte K blocks of image planes staged per SE row
+                                and unit (two tiles share them) */
 } morph_plan_info;
 
 /* --------------------------------------------------------------- calls */

@@ -34,7 +34,15 @@
 // one 128-byte K window (2 J + kw - 1 <= 128), a unit holds both (T = 2):
 // each A / B stage feeds the MMAs of both tiles, the second reading B from a
 // start address J bytes further, which halves the operand bytes per MMA; the
-// two accumulators then belong to the one unit.
+// two accumulators then belong to the one unit.  When they do not fit but
+// J >= 32 (flat or few-level SEs with wide rows), a unit may still hold two
+// tiles ("split"): tile 1's K window is tile 0's shifted by J bytes, so K
+// step ks of tile tt reads B byte 32 ks + tt J of the unit's window, i.e.
+// block (32 ks + tt J) / 128, with A block ks / 4 -- the block staged with
+// that B block or the one before it.  A row then stages ceil((J + 32 ksteps)
+// / 128) blocks for both tiles instead of nk per tile, the blocks past the
+// last A block carrying B only; each stage is released after the next
+// stage's MMAs.
 #include <algorithm>
 #include <cstring>
 
@@ -105,8 +113,9 @@ __device__ __forceinline__ bool epi_any_failed(bool failed) {
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// TT = 1 or 2: every problem of the launch has that many tiles per unit (the
-// compiler specialises the MMA issue loop); TT = 0: read T per problem.
+// TT = 1, 2 or 3: every problem of the launch has that unit kind (one tile,
+// two tiles in one K block, two split tiles; the compiler specialises the MMA
+// issue loop); TT = 0: read the kind per problem.
 template <int TT>
 __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_constant__ DirectLaunch dl) {
     extern __shared__ uint8_t smem_raw[];
@@ -157,19 +166,20 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
             const int* rb = P->meta;
             const int* rows = P->meta + (P->n_pass + 1) + P->n_pass * 8;
             const int xw = tc.j0 - (P->kw - 1) + P->ox + P->shift;   // plane column of the K window (32-aligned)
-            const int y0 = tc.i0 + P->oy, nk = P->nk, n_pass = P->n_pass;
+            const int y0 = tc.i0 + P->oy, nk = P->nk, nb = P->nb, n_pass = P->n_pass;
             for (int p = 0; ok && p < n_pass; ++p) {
                 const int q_end = rb[p + 1];
                 for (int q = rb[p]; ok && q < q_end; ++q) {
                     const int y = y0 - rows[q];
-                    for (int kc = 0; kc < nk; ++kc) {
+                    for (int kc = 0; kc < nb; ++kc) {
                         const uint32_t s = it % kStages;
                         const uint32_t ph = (it / kStages) & 1u;
                         if (!mbar_wait(empty0 + 8u * s, ph ^ 1u, abort_flag, dl.err)) { ok = false; break; }
                         const uint32_t fb = full0 + 8u * s;
-                        mbar_arrive_expect_tx(fb, kStageBytes);
+                        const bool with_a = kc < nk;   // split units stage one B block past the last A block
+                        mbar_arrive_expect_tx(fb, with_a ? kStageBytes : kStageB);
                         const uint32_t sa = ring0 + s * kStageBytes;
-                        tma_load_2d(sa, &P->tmA, 0, (q * nk + kc) * 128, fb);
+                        if (with_a) tma_load_2d(sa, &P->tmA, 0, (q * nk + kc) * 128, fb);
                         tma_load_4d(sa + kStageA, &P->tmB, xw + 128 * kc, 0, y, tc.n, fb);
                         ++it;
                     }
@@ -198,9 +208,11 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         for (long long t = blockIdx.x; ok && t < dl.total_tiles; t += gridDim.x) {
             const DirectProblemDev* P = direct_find(dl, t);
             const int* rb = P->meta;
-            const bool two = (TT == 0) ? (P->T == 2) : (TT == 2);
+            const bool two = (TT == 0) ? (P->T == 2) : (TT >= 2);
+            const bool split = (TT == 0) ? (P->split != 0) : (TT == 3);
             const uint64_t boff1 = static_cast<uint64_t>(P->J) >> 4;   // second tile: J bytes further along K
-            const int ksteps = P->ksteps, nk = P->nk;
+            const int sh1 = P->J >> 5;                                  // the same shift in 32-byte K steps
+            const int ksteps = P->ksteps, nk = P->nk, nb = P->nb;
             for (int p = 0; ok && p < P->n_pass; ++p) {
                 // a unit claims one slot (T = 1, alternating) or both (T = 2)
                 const uint32_t s0 = two ? 0u : next_slot;
@@ -212,16 +224,44 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + s0 * kDirectN;
-                uint32_t acc = 0;
+                uint32_t acc = 0, acc1 = 0;
                 const int q_end = rb[p + 1];
                 for (int q = rb[p]; ok && q < q_end; ++q) {
-                    for (int kc = 0; kc < nk; ++kc) {
+                    uint32_t s_prev = 0;
+                    for (int kc = 0; kc < nb; ++kc) {
                         const uint32_t s = it % kStages;
                         const uint32_t ph = (it / kStages) & 1u;
                         if (!mbar_wait(full0 + 8u * s, ph, abort_flag, dl.err)) { ok = false; break; }
                         tc_fence_after();
                         const uint64_t adesc = desc0 + static_cast<uint64_t>(s * (kStageBytes >> 4));
                         const uint64_t bdesc = adesc + static_cast<uint64_t>(kStageA >> 4);
+                        if (split) {
+                            // K step ks of tile tt reads B byte 32 (ks + tt J / 32) of the unit's window,
+                            // i.e. this block for the steps below; its A block is this stage's
+                            // (ks / 4 == kc) or the previous stage's
+                            const uint64_t adesc_prev = desc0 + static_cast<uint64_t>(s_prev * (kStageBytes >> 4));
+                            {
+                                const int lo = 4 * kc, hi = min(ksteps, 4 * kc + 4);
+                                for (int ks = lo; ks < hi; ++ks) {
+                                    tc_mma_f8(d_tmem, adesc + 2ull * (ks & 3), bdesc + 2ull * (ks & 3), idesc, acc);
+                                    acc = 1;
+                                }
+                            }
+                            {
+                                const int lo = max(0, 4 * kc - sh1), hi = min(ksteps, 4 * kc + 4 - sh1);
+                                for (int ks = lo; ks < hi; ++ks) {
+                                    const uint64_t ad = ((ks >> 2) == kc ? adesc : adesc_prev) + 2ull * (ks & 3);
+                                    tc_mma_f8(d_tmem + kDirectN, ad, bdesc + 2ull * ((ks + sh1) & 3), idesc, acc1);
+                                    acc1 = 1;
+                                }
+                            }
+                            // a stage's A block may still feed the next stage's tile-1 MMAs
+                            if (kc > 0) tc_commit(empty0 + 8u * s_prev);
+                            if (kc == nb - 1) tc_commit(empty0 + 8u * s);
+                            s_prev = s;
+                            ++it;
+                            continue;
+                        }
                         const int nks = min(4, ksteps - 4 * kc);
                         // advance the start addresses by 32 B of K inside the 128-B swizzled rows
                         if (two) {
@@ -263,7 +303,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         for (long long t = blockIdx.x; t < dl.total_tiles; t += gridDim.x) {
             const DirectProblemDev* P = direct_find(dl, t);
             const TileCoord tc = direct_tile(P, t);
-            const int J = P->J, G = P->G, rows_n = P->rows_n, Lpad = P->Lpad, T = (TT == 0) ? P->T : TT;
+            const int J = P->J, G = P->G, rows_n = P->rows_n, Lpad = P->Lpad, T = (TT == 0) ? P->T : (TT == 3 ? 2 : TT);
             const int g = m / J;
             const int* gw = P->meta + (P->n_pass + 1);
             bool failed = false;
@@ -464,13 +504,26 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     // two tiles per unit when both windows fit one 128-byte stage and the image is wide enough
     // (the second tile's K-steps read up to J + 32 ksteps bytes into the 128-byte rows)
     p->T = (2 * p->J + kw - 1 <= 128 && p->J + 32 * p->ksteps <= 128 && f->w > p->J) ? 2 : 1;
+    p->split = 0;
+    p->nb = p->nk;
     // K windows start at image column j0 - (kw - 1 - ox): shifting the planes by that amount mod 32
     // puts every window of a tile grid starting at column 0 on a 32-byte boundary (TMA needs 16;
     // 32 keeps each 128-byte box row on four whole L2 sectors)
     p->shift = (((kw - 1 - se->ox) % 32) + 32) % 32;
     p->e = 0;
-    p->tiles_x = (f->w + p->T * p->J - 1) / (p->T * p->J);
     p->tiles_y = (f->h + p->rows_n - 1) / p->rows_n;
+    if (p->T == 1 && p->J >= 32 && f->w > p->J && 2 * p->rows_n * p->J <= kRunEntries) {
+        // split two-tile units: fewer staged blocks per SE row for both tiles; J a multiple of 32
+        // keeps each K step inside one 128-byte row, both tiles' running pairs fit the run buffer
+        const int nb = (p->J + 32 * p->ksteps + 127) / 128;
+        const long long units = static_cast<long long>(f->n) * p->tiles_y * ((f->w + 2 * p->J - 1) / (2 * p->J));
+        if (nb < 2 * p->nk && units >= kDirectSplitMinUnits) {
+            p->T = 2;
+            p->split = 1;
+            p->nb = nb;
+        }
+    }
+    p->tiles_x = (f->w + p->T * p->J - 1) / (p->T * p->J);
     p->tiles = static_cast<long long>(f->n) * p->tiles_x * p->tiles_y;
     // meta: pass_row_begin[n_pass + 1], group_w[n_pass * 8], rows[]
     std::vector<int> rb(p->n_pass + 1, 0), gw(p->n_pass * 8, 0), rows;
@@ -577,13 +630,17 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
     d->shift = p.shift;
     d->erode = p.erode;
     d->T = p.T;
+    d->split = p.split;
+    d->nb = p.nb;
     d->tiles_x = p.tiles_x;
     d->tiles_y = p.tiles_y;
     d->tile_base = tile_base;
     d->tiles = p.tiles;
 }
 
-int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_T) {
+int direct_kind(const DirectProblemDev& d) { return d.split ? 3 : d.T; }
+
+int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_kind) {
     if (dl.total_tiles <= 0) return MORPH_OK;
     static int configured_device = -1;
     const int smem = direct_smem_bytes(kStages);
@@ -591,13 +648,15 @@ int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int u
         MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         configured_device = ctx->device;
     }
-    const int T = dl.many == nullptr ? dl.single.T : uniform_T;
+    const int kind = dl.many == nullptr ? direct_kind(dl.single) : (uniform_kind < 0 ? 0 : uniform_kind);
     long long grid = dl.total_tiles < ctx->num_sms ? dl.total_tiles : ctx->num_sms;
     prof_begin(ctx, st, "k_direct_fp8");
-    if (T == 1) k_direct_fp8<1><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
-    else if (T == 2) k_direct_fp8<2><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
+    if (kind == 1) k_direct_fp8<1><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
+    else if (kind == 2) k_direct_fp8<2><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
+    else if (kind == 3) k_direct_fp8<3><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
     else k_direct_fp8<0><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
     prof_end(ctx, st);
     ctx->launches += 1;

@@ -570,6 +570,8 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         out->passes = d.n_pass;
         out->tile_w = d.J;
         out->tile_h = d.rows_n;
+        out->unit_tiles = d.T;
+        out->unit_blocks = d.nb;
         out->est_flop = d.issued_flop;
         out->workspace_bytes = planes_bytes(f);
     } else if (route == ROUTE_NTT) {

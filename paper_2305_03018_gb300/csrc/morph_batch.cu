@@ -216,10 +216,10 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
             dl.single = b->probs[0];
             dl.many = nullptr;
         }
-        int uT = b->probs.empty() ? 0 : b->probs[0].T;
+        int kind = b->probs.empty() ? 0 : direct_kind(b->probs[0]);
         for (const auto& d : b->probs)
-            if (d.T != uT) uT = 0;
-        rc = launch_direct(ctx, dl, st, uT);
+            if (direct_kind(d) != kind) kind = 0;
+        rc = launch_direct(ctx, dl, st, kind);
         if (rc) return rc;
     }
     if (b->count_err && !b->fft_items.empty())

@@ -47,6 +47,7 @@ struct EncodeJob {
 
 // ------------------------------------------- FP8 tcgen05 direct route (Step 2)
 constexpr int kDirectMaxPasses = 32;
+constexpr long long kDirectSplitMinUnits = 2 * 152;   // split two-tile units only with two waves on 152 SMs
 constexpr int kDirectN = 256;        // MMA N: image rows x padded levels per tile
 constexpr int kDirectM = 128;        // MMA M: offset groups x output columns
 
@@ -61,7 +62,9 @@ struct DirectProblemDev {
     int n_pass, nk, ksteps, kw;
     int oy, ox, e, erode;
     int shift;              // plane column of image column 0 (TMA x = image column + shift)
-    int T;                  // horizontally adjacent tiles sharing each A/B stage (1 or 2)
+    int T;                  // horizontally adjacent tiles per unit (1 or 2)
+    int split;              // T = 2 with tile 1 one J-shift along a multi-block K window
+    int nb;                 // 128-byte K blocks staged per SE row and unit (nk, or nk + 1 when split)
     int tiles_x, tiles_y;   // units (of T tiles) across, tile rows down
     long long tile_base;    // first global tile of this problem
     long long tiles;        // tiles of this problem
@@ -76,7 +79,7 @@ struct DirectLaunch {
 };
 
 struct DirectPlan {
-    int L = 0, Lpad = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0, T = 1;
+    int L = 0, Lpad = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0, T = 1, split = 0, nb = 0;
     int kh = 0, kw = 0, oy = 0, ox = 0, e = 0, erode = 0, shift = 0;
     int h = 0, w = 0, nimg = 0, w_pad = 0;
     int tiles_x = 0, tiles_y = 0;
@@ -224,7 +227,9 @@ int launch_encode(morph_ctx* ctx, const EncodeJob* jobs, int njobs, long long to
 int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, DirectPlan* p);
 int plan_direct_host(const morph_image* f, const morph_se* se, int erode, DirectPlan* p);
 // uniform_T: tiles per unit shared by every problem of a batched launch (1 or 2), 0 if mixed
-int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_T = 0);
+// unit kind: 1 = one tile, 2 = two tiles in one K block, 3 = two split tiles; 0 = per problem
+int direct_kind(const DirectProblemDev& d);
+int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_kind = -1);
 int direct_smem_bytes(int stages);
 int direct_stages();
 void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,

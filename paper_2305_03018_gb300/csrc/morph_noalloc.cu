@@ -184,6 +184,7 @@ int plan_inline(const morph_image* f, const std::vector<uint8_t>& mask, const st
     p->J = 128 / p->G;
     p->ksteps = (p->J + kw - 1 + 31) / 32;
     p->nk = (p->J + kw - 1 + 127) / 128;
+    p->nb = p->nk;   // one tile per unit: every staged block carries its A block
     p->n_pass = (p->n_levels + p->G - 1) / p->G;
     const int a = (((kw - 1 - ox) % 16) + 16) % 16;
     p->e = (16 - a) % 16;

@@ -60,7 +60,8 @@ class morph_plan_info(ctypes.Structure):
                 ("f32_bound", ctypes.c_double), ("f64_bound", ctypes.c_double),
                 ("fft_nx", ctypes.c_int), ("fft_ny", ctypes.c_int), ("groups", ctypes.c_int),
                 ("passes", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
-                ("est_flop", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t)]
+                ("est_flop", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
+                ("unit_tiles", ctypes.c_int), ("unit_blocks", ctypes.c_int)]
 
 
 class morph_problem(ctypes.Structure):
