@@ -642,14 +642,13 @@ int direct_kind(const DirectProblemDev& d) { return d.split ? 3 : d.T; }
 
 int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_kind) {
     if (dl.total_tiles <= 0) return MORPH_OK;
-    static int configured_device = -1;
     const int smem = direct_smem_bytes(kStages);
-    if (configured_device != ctx->device) {
+    if (!kernels_ready(ctx->device, kGroupDirect)) {
         MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        configured_device = ctx->device;
+        mark_kernels_ready(ctx->device, kGroupDirect);
     }
     const int kind = dl.many == nullptr ? direct_kind(dl.single) : (uniform_kind < 0 ? 0 : uniform_kind);
     long long grid = dl.total_tiles < ctx->num_sms ? dl.total_tiles : ctx->num_sms;

@@ -801,9 +801,9 @@ static FftKernel range_for(int C) {
 }
 
 template <typename T>
-static int set_fft_smem() {
-    static bool done = false;
-    if (done) return MORPH_OK;
+static int set_fft_smem(int device) {
+    const KernelGroup grp = sizeof(T) == 4 ? kGroupFft32 : kGroupFft64;
+    if (kernels_ready(device, grp)) return MORPH_OK;
     const int big = 200 * 1024;
     for (int b = 1; b <= 32; b *= 2) {
         MORPH_CUDA_TRY(cudaFuncSetAttribute(rows_fwd_for<T>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -811,18 +811,17 @@ static int set_fft_smem() {
         MORPH_CUDA_TRY(cudaFuncSetAttribute(range_for<T>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
         if (b <= 16) MORPH_CUDA_TRY(cudaFuncSetAttribute(cols_for<T>(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     }
-    done = true;
+    mark_kernels_ready(device, grp);
     return MORPH_OK;
 }
 
-static int set_plane_smem() {
-    static bool done = false;
-    if (done) return MORPH_OK;
+static int set_plane_smem(int device) {
+    if (kernels_ready(device, kGroupFftPlane)) return MORPH_OK;
     const int big = kPlaneSmem;
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_plane_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_plane_cols<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_plane_cols<kPlaneCols>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    done = true;
+    mark_kernels_ready(device, kGroupFftPlane);
     return MORPH_OK;
 }
 
@@ -832,10 +831,10 @@ int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int
     int rc = plan_fft_tiles(f, se, prec, unproven, p);
     if (rc) return rc;
     const int Nx = p->ax.N, Ny = p->ay.N, K = p->K, Rf = p->Rf;
-    rc = set_plane_smem();
+    rc = set_plane_smem(ctx->device);
     if (rc) return rc;
-    if (prec == 4) rc = set_fft_smem<float>();
-    else rc = set_fft_smem<double>();
+    if (prec == 4) rc = set_fft_smem<float>(ctx->device);
+    else rc = set_fft_smem<double>(ctx->device);
     if (rc) return rc;
     const size_t cbytes = 2 * static_cast<size_t>(prec);
     MORPH_CUDA_TRY(cudaMalloc(&p->tw_x, Nx * cbytes));

@@ -780,9 +780,8 @@ static NttKernel range_for(int C) {
     }
 }
 
-static int set_ntt_smem() {
-    static bool done = false;
-    if (done) return MORPH_OK;
+static int set_ntt_smem(int device) {
+    if (kernels_ready(device, kGroupNtt)) return MORPH_OK;
     const int big = static_cast<int>(kNttSmemMax);
     for (int b = 1; b <= 64; b *= 2) {
         MORPH_CUDA_TRY(cudaFuncSetAttribute(rows_fwd_for(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -793,7 +792,7 @@ static int set_ntt_smem() {
         MORPH_CUDA_TRY(cudaFuncSetAttribute(range_for(b), cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_ntt_plane_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     MORPH_CUDA_TRY(cudaFuncSetAttribute(k_ntt_plane_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    done = true;
+    mark_kernels_ready(device, kGroupNtt);
     return MORPH_OK;
 }
 
@@ -831,7 +830,7 @@ int build_ntt_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, Ntt
     // the radix roots must have their exact orders (g primitive)
     if (npow(kW4, 2) != kP - 1 || kW3 == 1 || npow(kW3, 3) != 1 || kW5 == 1 || npow(kW5, 5) != 1)
         return MORPH_E_UNSUPPORTED;
-    rc = set_ntt_smem();
+    rc = set_ntt_smem(ctx->device);
     if (rc) return rc;
     const int Nx = p->ax.N, Ny = p->ay.N, Rf = p->Rf;
     if ((rc = upload(&p->tw_x, ntt_twiddles(Nx)))) return rc;

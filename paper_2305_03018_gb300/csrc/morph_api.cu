@@ -90,6 +90,21 @@ void prof_end(morph_ctx* ctx, cudaStream_t st) {
     cudaEventRecord(ctx->prof.back().b, st);
 }
 
+static std::mutex g_ready_mu;
+static std::vector<uint32_t> g_ready;   // per device: bit g = kernel group g set up
+
+bool kernels_ready(int device, KernelGroup group) {
+    std::lock_guard<std::mutex> lk(g_ready_mu);
+    return device >= 0 && device < static_cast<int>(g_ready.size()) && ((g_ready[device] >> group) & 1u);
+}
+
+void mark_kernels_ready(int device, KernelGroup group) {
+    std::lock_guard<std::mutex> lk(g_ready_mu);
+    if (device < 0) return;
+    if (device >= static_cast<int>(g_ready.size())) g_ready.resize(device + 1, 0u);
+    g_ready[device] |= 1u << group;
+}
+
 int ctx_workspace(morph_ctx* ctx, size_t bytes, void** out) {
     if (bytes <= ctx->ws_bytes) {
         *out = ctx->ws;

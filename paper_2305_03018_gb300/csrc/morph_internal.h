@@ -208,6 +208,14 @@ struct morph_ctx {
 
 namespace morph {
 
+// Kernel attributes (the dynamic shared-memory opt-in) belong to a device's
+// context: each group of kernels is set up once per device.  kernels_ready
+// tells whether `group` is set up on `device`; mark_kernels_ready records it
+// after the setup succeeded (a race only repeats the idempotent setup).
+enum KernelGroup { kGroupDirect = 0, kGroupFft32, kGroupFft64, kGroupFftPlane, kGroupNtt, kGroupCount };
+bool kernels_ready(int device, KernelGroup group);
+void mark_kernels_ready(int device, KernelGroup group);
+
 // Timing hook: event pair around one launch while profiling is on.
 void prof_begin(morph_ctx* ctx, cudaStream_t st, const char* name);
 void prof_end(morph_ctx* ctx, cudaStream_t st);
