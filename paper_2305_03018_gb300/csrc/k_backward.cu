@@ -157,16 +157,94 @@ __global__ void __launch_bounds__(kSeThreads) k_bwd_se_partial(BwdImage im, cons
     }
 }
 
-// grad_se[box] = sum of the partials of its tap in chunk order (fp64 accumulator); 0 off B.
-__global__ void k_bwd_se_final(const float* __restrict__ partial, int nchunks, const BwdTap* __restrict__ taps,
-                               int ntaps, int nbox, int sgn, float* __restrict__ grad_se) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) grad_se[b] = 0.f;
-    __syncthreads();
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntaps; t += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < nchunks; ++c) s += partial[static_cast<long long>(t) * nchunks + c];
-        grad_se[taps[t].box] = static_cast<float>(sgn * s);
+// Both gradients at once.  Every (source pixel p, tap y) term
+//   [f(p) + sgn b(y) = D(p + sgn y)] q(p + sgn y)
+// adds to grad_in(p) and to grad_se(y) (substituting x = p + sgn y in the
+// grad_se sum), so one pass over the terms serves both.  A CTA owns a chunk of
+// 256 M consecutive source pixels of one image in row-major order (thread k:
+// pixels k + 256 m of the chunk, m < M), keeps their f values
+// and grad_in sums in registers, and walks the taps in box order -- the order
+// k_bwd_input sums in; per tap each warp reduces its M-pixel sums with a fixed
+// shuffle tree into wsum[warp][tap], and the CTA adds its warps in order into
+// partial[tap][chunk] (taps <= kFusedMaxTaps).
+constexpr int kFusedMaxTaps = 1024;
+
+template <int SGN, int DT, int M>
+__global__ void __launch_bounds__(kSeThreads) k_bwd_fused(BwdImage im, const int32_t* __restrict__ D,
+                                                          const float* __restrict__ q,
+                                                          const BwdTap* __restrict__ taps, int ntaps,
+                                                          int chunks_per_img, int nchunks,
+                                                          float* __restrict__ partial, float* __restrict__ grad_in) {
+    extern __shared__ float wsum[];   // [kSeThreads / 32][ntaps]
+    const int chunk = blockIdx.x;
+    const int n = chunk / chunks_per_img;
+    const long long flat0 = static_cast<long long>(chunk - n * chunks_per_img) * (kSeThreads * M);
+    const long long npx = static_cast<long long>(im.h) * im.w;
+    const long long img0 = static_cast<long long>(n) * im.h;
+    int pi[M], pj[M], fp[M];
+    float acc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const long long flat = flat0 + threadIdx.x + kSeThreads * m;
+        const bool in = flat < npx;
+        pi[m] = in ? static_cast<int>(flat / im.w) : -(1 << 20);   // outside: every tap's row is off the image
+        pj[m] = in ? static_cast<int>(flat - static_cast<long long>(pi[m]) * im.w) : 0;
+        fp[m] = in ? load_px<DT>(im.f, n * im.batch_stride + pi[m] * im.row_stride + pj[m]) : 0;
+        acc[m] = 0.f;
     }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = 0; t < ntaps; ++t) {
+        const BwdTap tp = taps[t];
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int xi = pi[m] + SGN * tp.dy, xj = pj[m] + SGN * tp.dx;
+            if (static_cast<unsigned>(xi) < static_cast<unsigned>(im.h) &&
+                static_cast<unsigned>(xj) < static_cast<unsigned>(im.w)) {
+                const long long x = (img0 + xi) * im.w + xj;
+                if (fp[m] + SGN * tp.b == D[x]) {
+                    const float v = q[x];
+                    acc[m] += v;
+                    s += v;
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) wsum[warp * ntaps + t] = s;
+    }
+    if (grad_in) {
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            if (pi[m] >= 0) grad_in[(img0 + pi[m]) * im.w + pj[m]] = acc[m];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntaps; t += kSeThreads) {
+        float s = 0.f;
+        for (int w = 0; w < kSeThreads / 32; ++w) s += wsum[w * ntaps + t];
+        partial[static_cast<long long>(t) * nchunks + chunk] = s;
+    }
+}
+
+// grad_se[box of tap t] = the sum of tap t's partials in fp64, one CTA per tap:
+// thread k adds chunks k, k + 256, ... in order, then a fixed tree over the
+// threads (boxes off B are zeroed beforehand on the same stream).
+constexpr int kFinalThreads = 256;
+
+__global__ void __launch_bounds__(kFinalThreads) k_bwd_se_final(const float* __restrict__ partial, int nchunks,
+                                                                const BwdTap* __restrict__ taps, int sgn,
+                                                                float* __restrict__ grad_se) {
+    __shared__ double red[kFinalThreads];
+    const int t = blockIdx.x;
+    const float* pt = partial + static_cast<long long>(t) * nchunks;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < nchunks; c += kFinalThreads) s += pt[c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kFinalThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) grad_se[taps[t].box] = static_cast<float>(sgn * red[0]);
 }
 
 }  // namespace morph
@@ -193,6 +271,20 @@ static BwdInputKernel input_kernel(int dt) {
     return dt == MORPH_U8 ? k_bwd_input<SGN, MORPH_U8> : dt == MORPH_U16 ? k_bwd_input<SGN, MORPH_U16>
                                                                           : k_bwd_input<SGN, MORPH_I32>;
 }
+typedef void (*BwdFusedKernel)(BwdImage, const int32_t*, const float*, const BwdTap*, int, int, int, float*,
+                               float*);
+
+template <int SGN, int DT>
+static BwdFusedKernel fused_kernel_m(int M) {
+    return M >= 8 ? k_bwd_fused<SGN, DT, 8> : M == 4 ? k_bwd_fused<SGN, DT, 4>
+                                            : M == 2 ? k_bwd_fused<SGN, DT, 2> : k_bwd_fused<SGN, DT, 1>;
+}
+template <int SGN>
+static BwdFusedKernel fused_kernel(int dt, int M) {
+    return dt == MORPH_U8 ? fused_kernel_m<SGN, MORPH_U8>(M) : dt == MORPH_U16 ? fused_kernel_m<SGN, MORPH_U16>(M)
+                                                                               : fused_kernel_m<SGN, MORPH_I32>(M);
+}
+
 template <int SGN>
 static BwdSeKernel se_kernel(int dt) {
     return dt == MORPH_U8 ? k_bwd_se_partial<SGN, MORPH_U8> : dt == MORPH_U16 ? k_bwd_se_partial<SGN, MORPH_U16>
@@ -216,12 +308,43 @@ static size_t share_bytes(const morph_image* f) {
     return (total * sizeof(float) + 255) & ~size_t(255);
 }
 
+// How the SE-gradient partial sums are laid out: the fused kernel for SEs of up
+// to kFusedMaxTaps taps (chunks of 256 M consecutive pixels, M the largest of
+// 8, 4, 2, 1 that still gives four CTAs per SM of a 152-SM GB300, where the
+// batch allows), else the pixel-chunked gather (chunks of <= 8192 pixels).
+struct BwdLayout {
+    bool fused = false;
+    int M = 1;
+    int chunks_per_img = 0;
+    SeChunks ch{};
+    long long nchunks = 0;
+};
+
+static BwdLayout bwd_layout(const morph_image* f, int ntaps) {
+    BwdLayout L;
+    const long long npx = static_cast<long long>(f->h) * f->w;
+    L.fused = ntaps > 0 && ntaps <= kFusedMaxTaps;
+    if (L.fused) {
+        L.M = 8;
+        while (L.M > 1 && npx * f->n / (kSeThreads * L.M) < 4LL * 152) L.M /= 2;
+        const long long per = (npx + kSeThreads * L.M - 1) / (kSeThreads * L.M);
+        if (per > (1LL << 30)) L.fused = false;
+        else {
+            L.chunks_per_img = static_cast<int>(per);
+            L.nchunks = per * f->n;
+            return L;
+        }
+    }
+    L.ch = se_chunks(f);
+    L.nchunks = static_cast<long long>(f->n) * L.ch.cy * L.ch.cx;
+    return L;
+}
+
 size_t morph::backward_workspace_bytes(const morph_image* f, const morph_se* b) {
     int ntaps = 0;
     for (int t = 0; t < b->kh * b->kw; ++t) ntaps += b->mask[t] ? 1 : 0;
-    const SeChunks ch = se_chunks(f);
-    const size_t nchunks = static_cast<size_t>(f->n) * ch.cy * ch.cx;
-    return share_bytes(f) + static_cast<size_t>(ntaps) * nchunks * sizeof(float);
+    const BwdLayout L = bwd_layout(f, ntaps);
+    return share_bytes(f) + static_cast<size_t>(ntaps) * static_cast<size_t>(L.nchunks) * sizeof(float);
 }
 
 static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b, const int32_t* D,
@@ -272,11 +395,12 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
     }
     BwdImage im{f->data, f->dtype, f->n, f->h, f->w, f->row_stride, f->batch_stride, sgn};
     const long long total = static_cast<long long>(f->n) * f->h * f->w;
-    // chunks of the SE-gradient sums: RB rows x CB columns of one image
-    const SeChunks ch = se_chunks(f);
-    const long long nchunks_ll = static_cast<long long>(f->n) * ch.cy * ch.cx;
-    if (nchunks_ll > (1LL << 30)) return MORPH_E_UNSUPPORTED;
-    const int nchunks = static_cast<int>(nchunks_ll);
+    // chunks of the SE-gradient sums
+    const BwdLayout lay = bwd_layout(f, plan->ntaps);
+    if (lay.nchunks > (1LL << 30)) return MORPH_E_UNSUPPORTED;
+    const int nchunks = static_cast<int>(lay.nchunks);
+    const SeChunks ch = lay.ch;
+    const bool fused = grad_se && lay.fused;
     // workspace: q (one float per pixel), then the partial sums
     const size_t q_bytes = share_bytes(f);
     const size_t part_bytes = grad_se ? static_cast<size_t>(plan->ntaps) * nchunks * sizeof(float) : 0;
@@ -292,7 +416,19 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
         ctx->launches += 1;
         MORPH_CUDA_TRY(cudaGetLastError());
     }
-    if (grad_in) {
+    if (fused) {
+        // one pass over the (pixel, tap) terms for both gradients
+        float* partial = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + q_bytes);
+        const size_t smem = sizeof(float) * (kSeThreads / 32) * plan->ntaps;
+        prof_begin(ctx, st, "k_bwd_fused");
+        const BwdFusedKernel kf = sgn > 0 ? fused_kernel<1>(f->dtype, lay.M) : fused_kernel<-1>(f->dtype, lay.M);
+        kf<<<nchunks, kSeThreads, smem, st>>>(im, D, q, plan->d_taps, plan->ntaps, lay.chunks_per_img, nchunks,
+                                              partial, grad_in);
+        prof_end(ctx, st);
+        ctx->launches += 1;
+        MORPH_CUDA_TRY(cudaGetLastError());
+    }
+    if (grad_in && !fused) {
         const int bx = std::min(256, ((f->w + 31) / 32) * 32);
         const long long rows = static_cast<long long>(f->n) * f->h;
         dim3 grid(static_cast<unsigned>((f->w + bx - 1) / bx), static_cast<unsigned>(std::min<long long>(rows, 65535)));
@@ -306,8 +442,8 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
     if (grad_se) {
         const int nbox = b->kh * b->kw;
         float* partial = nullptr;
-        if (plan->ntaps > 0) {
-            partial = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + q_bytes);
+        if (plan->ntaps > 0) partial = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + q_bytes);
+        if (plan->ntaps > 0 && !fused) {
             dim3 grid(nchunks, (plan->ntaps + kSeTaps - 1) / kSeTaps);
             prof_begin(ctx, st, "k_bwd_se_partial");
             const BwdSeKernel kse = sgn > 0 ? se_kernel<1>(f->dtype) : se_kernel<-1>(f->dtype);
@@ -316,11 +452,14 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
             ctx->launches += 1;
             MORPH_CUDA_TRY(cudaGetLastError());
         }
-        prof_begin(ctx, st, "k_bwd_se_final");
-        k_bwd_se_final<<<1, 1024, 0, st>>>(partial, nchunks, plan->d_taps, plan->ntaps, nbox, sgn, grad_se);
-        prof_end(ctx, st);
-        ctx->launches += 1;
-        MORPH_CUDA_TRY(cudaGetLastError());
+        MORPH_CUDA_TRY(cudaMemsetAsync(grad_se, 0, sizeof(float) * static_cast<size_t>(nbox), st));
+        if (plan->ntaps > 0) {
+            prof_begin(ctx, st, "k_bwd_se_final");
+            k_bwd_se_final<<<plan->ntaps, kFinalThreads, 0, st>>>(partial, nchunks, plan->d_taps, sgn, grad_se);
+            prof_end(ctx, st);
+            ctx->launches += 1;
+            MORPH_CUDA_TRY(cudaGetLastError());
+        }
     }
     return MORPH_OK;
 }

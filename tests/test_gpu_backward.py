@@ -2,8 +2,10 @@
 
 Tolerance from the arithmetic: the library sums fp32 terms g(x)/cD(x).
 grad_in(p) adds at most |B| terms in sequence: |error| <= (|B| + 2) u S(p);
-grad_se(y) adds each 8192-pixel chunk with a depth of at most 32 + 5 + 8
-additions, then the chunks in fp64: |error| <= 48 u S(y) + u |grad_se(y)|,
+grad_se(y) adds each chunk of pixels with a depth of at most 32 + 5 + 8
+additions (a thread's pixels, a warp tree, a CTA's warps; up to 1024 taps the
+fused kernel's depth is 8 + 5 + 8), then the chunks in fp64:
+|error| <= 48 u S(y) + u |grad_se(y)|,
 where u = 2^-24 and S is the same sum taken over |g| (the oracle with |g|).
 """
 import numpy as np
@@ -114,11 +116,21 @@ def test_erosion_backward_irregular_se_with_ties():
 
 @pytest.mark.parametrize("shape", [(2, 1, 5, 9000), (1, 1, 300, 1), (3, 1, 70, 33), (1, 1, 1, 40)])
 def test_chunking_edge_shapes(shape):
-    # SE-gradient chunks are rows x columns of one image: rows wider than a chunk,
-    # one-column images, ragged chunk tails
+    # SE-gradient chunks (runs of consecutive pixels, or rows x columns blocks above 1024
+    # taps): rows wider than a chunk, one-column images, ragged chunk tails
     g = wl.rng(sum(shape))
     x = g.integers(0, 8, size=shape).astype(np.float32)
     se = wl.se_random(g, 3, 5, 0.7, 3, origin=(1, 2))
     up = g.standard_normal(shape).astype(np.float32)
     _check(x, se.offset.astype(np.float32), se.mask, se.origin, 8, up)
     _check_erode(x, se.offset.astype(np.float32), se.mask, se.origin, 8, up)
+
+
+def test_more_than_1024_taps():
+    # above 1024 taps the two gradients come from the two gathers instead of the fused pass
+    g = wl.rng(35)
+    x = g.integers(0, 6, size=(2, 1, 48, 61)).astype(np.float32)
+    se = wl.se_full_random(g, 33, 3)
+    up = g.standard_normal(x.shape).astype(np.float32)
+    _check(x, se.offset.astype(np.float32), se.mask, se.origin, 6, up)
+    _check_erode(x, se.offset.astype(np.float32), se.mask, se.origin, 6, up)

@@ -163,7 +163,7 @@ def test_data_error_reported(ctx):
     ctx.check()                                  # the error word was cleared
 
 
-def test_workspace_size_matches_plan_and_is_host_only():
+def test_workspace_size_matches_plan_and_is_host_only(bwd_chunks):
     from paper_2305_03018_gb300.morph import get_context
     ctx = get_context(0)
     g = wl.rng(61)
@@ -176,8 +176,7 @@ def test_workspace_size_matches_plan_and_is_host_only():
     assert ctx.workspace_size(f, 64, se, op=0, method="direct_fp8") == 2 * 200 * 64 * 352
     # backward: one float share per pixel (rounded to 256 B) plus one partial sum per (tap, chunk)
     ntaps = int(np.count_nonzero(se.mask))
-    chunks = 2 * ((200 + (8192 // 300) - 1) // (8192 // 300))
-    exp = ((2 * 200 * 300 * 4 + 255) // 256) * 256 + ntaps * chunks * 4
+    exp = ((2 * 200 * 300 * 4 + 255) // 256) * 256 + ntaps * bwd_chunks(2, 200, 300, ntaps) * 4
     assert ctx.workspace_size(f, 64, se, op=2) == exp == ctx.workspace_size(f, 64, se, op=3)
 
 

@@ -30,18 +30,21 @@ def _ws(im, se, op, method="auto"):
     return M.morph_workspace_size(None, im, sv.c, op, M.make_opts(method))
 
 
-def test_direct_and_backward_sizes_follow_their_layouts():
+def test_direct_and_backward_sizes_follow_their_layouts(bwd_chunks):
     g = wl.rng(61)
     se = wl.se_random(g, 9, 7, 0.6, 5)
     im = _img(2, 200, 300, 64)
     # indicator planes: n h L round32(w + 31) bytes (room for the column shift that aligns K windows)
     assert _ws(im, se, 0, "direct_fp8") == _ws(im, se, 1, "direct_fp8") == 2 * 200 * 64 * 352
-    # backward: a float share per pixel (256-byte rounded) + a partial sum per (tap, chunk of <= 8192 px)
+    # backward: a float share per pixel (256-byte rounded) + a partial sum per (tap, chunk)
     ntaps = int(np.count_nonzero(se.mask))
-    rows_per_chunk = 8192 // 300
-    chunks = 2 * -(-200 // rows_per_chunk)
-    exp = -(-2 * 200 * 300 * 4 // 256) * 256 + ntaps * chunks * 4
+    exp = -(-2 * 200 * 300 * 4 // 256) * 256 + ntaps * bwd_chunks(2, 200, 300, ntaps) * 4
     assert _ws(im, se, 2) == _ws(im, se, 3) == exp
+    # more than 1024 taps: the pixel-chunked gather's layout
+    big = wl.se_full_random(g, 33, 3)
+    exp = -(-2 * 200 * 300 * 4 // 256) * 256 + 33 * 33 * bwd_chunks(2, 200, 300, 33 * 33) * 4
+    assert _ws(im, big, 2) == exp
+
 
 
 def test_transform_routes_plan_on_the_host():
