@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(kSeThreads) k_bwd_fused(BwdImage im, const int
     const long long npx = static_cast<long long>(im.h) * im.w;
     const long long img0 = static_cast<long long>(n) * im.h;
     int pi[M], pj[M], fp[M];
+    long long px[M];   // flat index of the pixel in D and q
     float acc[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -189,20 +190,23 @@ __global__ void __launch_bounds__(kSeThreads) k_bwd_fused(BwdImage im, const int
         const bool in = flat < npx;
         pi[m] = in ? static_cast<int>(flat / im.w) : -(1 << 20);   // outside: every tap's row is off the image
         pj[m] = in ? static_cast<int>(flat - static_cast<long long>(pi[m]) * im.w) : 0;
+        px[m] = img0 * im.w + flat;
         fp[m] = in ? load_px<DT>(im.f, n * im.batch_stride + pi[m] * im.row_stride + pj[m]) : 0;
         acc[m] = 0.f;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int t = 0; t < ntaps; ++t) {
         const BwdTap tp = taps[t];
+        // the tap as row / column steps, a flat-index step and a level shift
+        const int sy = SGN * tp.dy, sx = SGN * tp.dx, sb = SGN * tp.b;
+        const long long so = static_cast<long long>(sy) * im.w + sx;
         float s = 0.f;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            const int xi = pi[m] + SGN * tp.dy, xj = pj[m] + SGN * tp.dx;
-            if (static_cast<unsigned>(xi) < static_cast<unsigned>(im.h) &&
-                static_cast<unsigned>(xj) < static_cast<unsigned>(im.w)) {
-                const long long x = (img0 + xi) * im.w + xj;
-                if (fp[m] + SGN * tp.b == D[x]) {
+            if (static_cast<unsigned>(pi[m] + sy) < static_cast<unsigned>(im.h) &&
+                static_cast<unsigned>(pj[m] + sx) < static_cast<unsigned>(im.w)) {
+                const long long x = px[m] + so;
+                if (fp[m] + sb == D[x]) {
                     const float v = q[x];
                     acc[m] += v;
                     s += v;
