@@ -720,6 +720,10 @@ int plan_ntt_tiles(const morph_image* f, const morph_se* se, NttPlan* p) {
     // column / pixel groups small enough for two CTAs per SM; 512 threads for big groups
     p->colgroup = 16;
     while (p->colgroup > 1 && smem_pitched(Ny, p->colgroup) > kNttSmemHalf) p->colgroup /= 2;
+    // 8 columns instead of 16 where 8 fit a quarter of shared memory (five CTAs per SM instead
+    // of two: the 576-point columns of a 512^2 image with a 64^2 filter ran 1.73 -> 1.60 ms);
+    // fewer than two columns per CTA was slower (2048-point columns: 4.37 -> 4.93 ms)
+    if (p->colgroup == 16 && smem_pitched(Ny, 8) <= 56 * 1024) p->colgroup = 8;
     p->pixgroup = ntt_pixgroup(p->Rf);
     p->col_threads = Ny * p->colgroup >= 8192 ? 512 : 256;
     p->pix_threads = p->Rf * p->pixgroup >= 8192 ? 512 : 256;
