@@ -1,4 +1,5 @@
-"""The allocation-free entry point (morph_run_noalloc) against the regular one.
+"""The allocation-free entry point (morph_run_noalloc) against the oracle and
+the regular entry point.
 
 Some callers cannot allocate device memory; morph_run_noalloc serves them
 from a fixed 64 MiB device array.  This file is collected last so that a run
@@ -8,6 +9,7 @@ pass alone in a fresh process and after the other tests.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2305_03018_gb300 import workloads as wl
 
 torch = pytest.importorskip("torch")
@@ -45,6 +47,10 @@ def test_noalloc_matches_regular_entry_point_on_two_calls_in_a_row():
         assert int(status.item()) == 0
         assert torch.equal(out, ref)             # bit-exact, as every parity test here
         assert torch.equal(cnt, ref_c)
+        ofn = oracle.dilate if op == 0 else oracle.erode
+        oD, oC = ofn(f_np, L, se.mask, se.offset, se.origin)
+        assert np.array_equal(out.cpu().numpy(), oD)
+        assert np.array_equal(cnt.cpu().numpy(), oC)
 
 
 def test_noalloc_rejects_problems_larger_than_its_scratch():
