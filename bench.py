@@ -46,6 +46,8 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FFT-form comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra keys for the 4096x4096 L=256 image and the 512-problem batch")
     ap.add_argument("--cpu-rows", type=int, default=0,
                     help="cpu_baseline: image rows per operation on all cores (0 = all rows)")
     ap.add_argument("--cpu-rows-single", type=int, default=96,
@@ -160,6 +162,56 @@ def _profile_traffic():
         return None, "summary without dram_bytes_per_launch"
 
 
+# One tcgen05 MMA of the direct route: M = 128, N = 256, K = 32 (FP8), 2 FLOP per multiply-add.
+MMA_FLOP = 2.0 * 128 * 256 * 32
+
+
+def _method_flop(taps: int, L: int, pixels: int) -> float:
+    """The method's own work for one operation: Step 2 (Sec. 3, Eq. Obs7)
+    contracts each output pixel's |B| taps with the one-hot image umbra over
+    the L grey levels, 2 |B| L FLOP per output pixel."""
+    return 2.0 * taps * L * pixels
+
+
+def _fp8_peak():
+    """Dense FP8 peak: the measured bf16 GEMM rate x 2 (the nominal FP8/bf16
+    dense ratio).  The burst figure is the denominator: the timed region is
+    well under a second and runs at the maximum SM clock, while the sustained
+    GEMM figure was taken at a power-capped median clock."""
+    mp, src = _peaks()
+    burst = 2.0 * float(mp.get("bf16_tflops", 1900.0))
+    sus = 2.0 * float(mp.get("bf16_tflops_sustained", mp.get("bf16_tflops", 1700.0)))
+    clk = (mp.get("clocks_under_load") or {}).get("sm_mhz_median")
+    return burst, sus, clk, src
+
+
+def _roofline(kt, flop, method_flop, steps, issued):
+    """Roofline of k_direct_fp8 on the method's work (2 |B| L FLOP per pixel),
+    with the MMAs the kernel actually issued (device counter) beside it."""
+    kd = kt.get("k_direct_fp8", (0, 0.0))
+    peak, peak_sus, clk, src = _fp8_peak()
+    secs = kd[1] * 1e-3
+    work = steps * sum(method_flop.values())
+    achieved = work / secs / 1e12 if secs > 0 else None
+    issued_tf = issued / secs / 1e12 if secs > 0 and issued else None
+    traffic, traffic_src = _profile_traffic()
+    ratio = {k: flop[k] / method_flop[k] for k in flop if method_flop.get(k)}
+    return {"kernel": "k_direct_fp8", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "work": "method: 2 |B| L FLOP per output pixel (Step 2, Eq. Obs7, one-hot umbra dense over L)",
+            "peak_source": f"{src} bf16 burst x 2 (nominal fp8/bf16 dense ratio)",
+            "frac_of_sustained": (achieved / peak_sus) if achieved else None,
+            "sustained_peak": peak_sus, "sustained_peak_sm_mhz": clk,
+            "issued": {"achieved": issued_tf, "frac": (issued_tf / peak) if issued_tf else None,
+                       "flop_per_step": issued / steps if steps else None,
+                       "source": "MMA instructions counted on the device x 2 x 128 x 256 x 32",
+                       "planned_issued_over_method": ratio},
+            "traffic_source": traffic_src,
+            "launches": kd[0], "avg_launch_ms": kd[1] / kd[0] if kd[0] else None,
+            "method_flop_per_launch": dict(method_flop),
+            "kernel_ms_share": {k: v[1] / max(1e-9, sum(x[1] for x in kt.values())) for k, v in kt.items()}}
+
+
 def max_over_ranks(x: float, dist, device) -> float:
     """The slowest rank's time (every rank must call it)."""
     if dist is None:
@@ -250,10 +302,11 @@ def run_ours(args, ws, rank, local):
     for _ in range(max(3, args.warmup)):
         step(f_dev)
     ctx.check()
-    flop = {}
+    flop, method_flop = {}, {}
     for p in probs:
         info = ctx.plan(f_dev, L, p.se, op=0 if p.op == "dilate" else 1, method="direct_fp8")
         flop[p.name] = info.est_flop
+        method_flop[p.name] = _method_flop(p.se.taps, L, n * h * w)
 
     def barrier():
         if dist is not None:
@@ -265,6 +318,7 @@ def run_ours(args, ws, rank, local):
     time.sleep(0.3)
     ctx.profile(True)
     launches0 = ctx.launches()
+    issued0 = ctx.mma_count()
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -275,6 +329,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     barrier()
     launches = ctx.launches() - launches0
+    issued = (ctx.mma_count() - issued0) * MMA_FLOP
     ctx.profile(False)
     ms = ev0.elapsed_time(ev1) / args.steps
     kt = ctx.profile_read()
@@ -356,19 +411,7 @@ def run_ours(args, ws, rank, local):
         return 0
 
     # ---- roofline of the dominant kernel (tensor pipe, FP8 dense)
-    mp, src = _peaks()
-    kd = kt.get("k_direct_fp8", (0, 0.0))
-    total_flop = args.steps * sum(flop.values())
-    achieved = total_flop / (kd[1] * 1e-3) / 1e12 if kd[1] > 0 else None
-    peak = 2.0 * float(mp.get("bf16_tflops_sustained", mp.get("bf16_tflops")))
-    traffic, traffic_src = _profile_traffic()
-    roof = {"kernel": "k_direct_fp8", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "peak_source": f"{src} bf16 sustained x 2 (nominal fp8/bf16 dense ratio)",
-            "traffic_source": traffic_src,
-            "launches": kd[0], "avg_launch_ms": kd[1] / kd[0] if kd[0] else None,
-            "flop_per_launch": {k: v for k, v in flop.items()},
-            "kernel_ms_share": {k: v[1] / max(1e-9, sum(x[1] for x in kt.values())) for k, v in kt.items()}}
+    roof = _roofline(kt, flop, method_flop, args.steps, issued)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -385,8 +428,16 @@ def run_ours(args, ws, rank, local):
                     "serial_value": job_throughput(px_per_step, ws, serial_ms)}}
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 only
+    if ws == 1 and not args.no_extra:
+        line["configs_extra"] = _extra_configs(ctx, args)
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(args, probs, outs)
+        # values and top counts of the timed route, compared with the oracle's on every pixel
+        got = []
+        for p in probs:
+            d, c = (ctx.dilate if p.op == "dilate" else ctx.erode)(f_dev, L, p.se, method="direct_fp8", count=True)
+            got.append((d.cpu().numpy(), c.cpu().numpy()))
+        ctx.check()
+        line["cpu_baseline"] = _cpu_baseline(args, probs, got)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -468,11 +519,11 @@ def _cpu_baseline(args, probs, outs):
     cores = oracle.max_threads()
     t0 = time.perf_counter()
     exact = True
-    for p, o in zip(probs, outs):
+    for p, (gd, gc) in zip(probs, outs):
         fn = oracle.dilate if p.op == "dilate" else oracle.erode
-        ref, _ = fn(p.f, p.L, p.se.mask, p.se.offset, p.se.origin, rows=(r0, r0 + rows), nthreads=0)
-        got = o[:, r0:r0 + rows].cpu().numpy()
-        exact &= bool(np.array_equal(got, ref[:, r0:r0 + rows]))
+        ref, ref_c = fn(p.f, p.L, p.se.mask, p.se.offset, p.se.origin, rows=(r0, r0 + rows), nthreads=0)
+        exact &= bool(np.array_equal(gd[:, r0:r0 + rows], ref[:, r0:r0 + rows]))
+        exact &= bool(np.array_equal(gc[:, r0:r0 + rows], ref_c[:, r0:r0 + rows]))
     dt = time.perf_counter() - t0
     srows = min(H, max(1, args.cpu_rows_single))
     s0 = (H - srows) // 2
@@ -484,10 +535,152 @@ def _cpu_baseline(args, probs, outs):
     whole = "all rows" if rows == H else f"rows {r0}..{r0 + rows - 1}"
     return {"value": 4 * rows * W / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{whole} of each of the 4 operations ({4 * rows * W} px, {dt:.1f} s on {cores} threads)",
-            "parity_on_sample": "bit-exact" if exact else "MISMATCH",
+            "parity_on_sample": ("bit-exact (values and top counts)" if exact else "MISMATCH"),
             "single_thread": {"value": 4 * srows * W / dt1 / 1e6, "unit": UNIT, "cores": 1,
                               "sample": f"rows {s0}..{s0 + srows - 1} of each of the 4 operations "
                                         f"({4 * srows * W} px, {dt1:.1f} s)"}}
+
+
+# ------------------------------------------- extra keys of the default run
+def _extra_configs(ctx, args):
+    """The largest single-GPU configuration (4096x4096, L = 256, 31x31 convex
+    SE, offsets U[0, 15]: every exact form, each with its measured max count
+    error) and the 512-problem uneven batch (AUTO, one captured graph), each
+    timed for a few steps with CUDA events; every form's output is compared
+    with the FP8 route's."""
+    import torch
+
+    from paper_2305_03018_gb300 import workloads as wl
+    steps = 3
+    res = {}
+    # ---- 4096 x 4096, L = 256
+    p = wl.c3_full_tonal()
+    f = torch.from_numpy(p.f).cuda()
+    px = p.f.size
+    stream = torch.cuda.current_stream()
+    c3 = {"workload": "4096x4096 smooth L=256, 31x31 convex SE (%d taps) offsets U[0,15], dilation" % p.se.taps,
+          "forms": {}}
+    ref = None
+    for name, method in (("direct_fp8", "direct_fp8"), ("ntt", "ntt"), ("fft_f32", "fft_f32"),
+                         ("fft_f64", "fft_f64")):
+        err = torch.zeros(1, dtype=torch.float32, device="cuda")
+        kw = {"count_err": err} if method.startswith("fft") else {}
+        try:
+            out, cnt = ctx.dilate(f, p.L, p.se, method=method, count=True, **kw)
+        except Exception as e:                      # e.g. FP32 refused by its bound
+            c3["forms"][name] = {"value": None, "note": str(e)[:120]}
+            continue
+        torch.cuda.synchronize()
+        ctx.check()
+        if ref is None:
+            ref = (out, cnt)
+        exact = bool(torch.equal(out, ref[0])) and bool(torch.equal(cnt, ref[1]))
+        ctx.profile(True)
+        i0 = ctx.mma_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.dilate(f, p.L, p.se, method=method, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        issued = (ctx.mma_count() - i0) * MMA_FLOP / steps
+        kt = ctx.profile_read()
+        ctx.profile(False)
+        ctx.check()
+        ms = e0.elapsed_time(e1) / steps
+        row = {"value": px / (ms * 1e-3) / 1e6, "ms_per_op": ms, "exact_vs_fp8": exact}
+        info = ctx.plan(f, p.L, p.se, method=method)
+        if method.startswith("fft"):
+            row["max_count_err"] = float(err.item())
+            row["a_priori_bound"] = info.f32_bound if method == "fft_f32" else info.f64_bound
+            row["proven"] = row["a_priori_bound"] < 0.5
+        else:
+            row["max_count_err"] = 0.0
+        if method == "direct_fp8" and "k_direct_fp8" in kt:
+            peak = _fp8_peak()[0]
+            ksec = kt["k_direct_fp8"][1] * 1e-3 / steps
+            work = _method_flop(p.se.taps, p.L, px)
+            row["roofline"] = {"achieved": work / ksec / 1e12, "peak": peak, "unit": "TFLOP/s",
+                               "frac": work / ksec / 1e12 / peak,
+                               "issued_frac": issued / ksec / 1e12 / peak,
+                               "issued_over_method": issued / work,
+                               "work": "method: 2 |B| L FLOP per output pixel"}
+        c3["forms"][name] = row
+    c3["value_best"] = max((r["value"] for r in c3["forms"].values() if r.get("value")), default=None)
+    res["c3_4096x4096_L256"] = c3
+    del f, ref
+    torch.cuda.empty_cache()
+    # ---- 512 uneven problems, AUTO routes, one captured graph
+    probs = wl.c5_batch()
+    items, pxs = [], 0
+    for q in probs:
+        ft = torch.from_numpy(q.f).cuda()
+        items.append((ft, q.L, q.se, q.op, torch.empty(ft.shape, dtype=torch.int32, device="cuda"),
+                      torch.empty(ft.shape, dtype=torch.int32, device="cuda")))
+        pxs += ft.numel()
+    t0 = time.perf_counter()
+    bt = ctx.capture_batch(items, method="auto")
+    plan_s = time.perf_counter() - t0
+    l0 = ctx.launches()
+    bt.launch()
+    torch.cuda.synchronize()
+    graph_launches = ctx.launches() - l0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        bt.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = e0.elapsed_time(e1) / steps
+    routes = {}
+    for q, it in zip(probs, items):
+        m = ctx.plan(it[0], q.L, q.se, op=0 if q.op == "dilate" else 1, method="auto").method
+        nm = {0: "empty", 1: "direct_fp8", 2: "fft_f32", 3: "fft_f64", 4: "ntt"}.get(m, str(m))
+        routes[nm] = routes.get(nm, 0) + 1
+    res["c5_512_uneven"] = {"workload": "512 uneven problems, sides U[64,1024], L in {16,64,256}, SE 3..63, "
+                                        "one captured graph (AUTO routes)",
+                            "value": pxs / (ms * 1e-3) / 1e6, "ms_per_replay": ms, "pixels": pxs,
+                            "graph_launches": graph_launches, "plan_and_capture_s": plan_s,
+                            "routes_as_single_calls": routes}
+    bt.close()
+    del items
+    torch.cuda.empty_cache()
+    # ---- the learnable layer: 64x1x128x128, L = 32, 9x9 SE, forward + backward through autograd
+    from paper_2305_03018_gb300.autograd import dilate
+    c = wl.c4_layer()
+    x = torch.from_numpy(c.x).cuda().requires_grad_(True)
+    b = torch.from_numpy(c.b).cuda().requires_grad_(True)
+    gup = torch.from_numpy(c.g).cuda()
+
+    def fwd_bwd():
+        x.grad = None
+        b.grad = None
+        dilate(x, b, c.L, None, c.origin).backward(gup)
+
+    for _ in range(3):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for _ in range(10):
+        fwd_bwd()
+    e1.record()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / 10
+    kt = ctx.profile_read()
+    ctx.profile(False)
+    ctx.check()
+    ms = e0.elapsed_time(e1) / 10
+    busy = sum(v[1] for v in kt.values()) / 10
+    res["c4_layer_64x1x128x128"] = {"workload": "64x1x128x128 L=32, learnable 9x9 SE offsets U[0,7], forward + "
+                                                "backward through torch.autograd",
+                                    "value": x.numel() / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                                    "gpu_kernel_ms_per_step": busy, "gpu_busy_frac": busy / ms if ms else None,
+                                    "kernel_ms_per_step": {k: v[1] / 10 for k, v in kt.items()}}
+    return res
 
 
 # ------------------------------------------------------- other configurations
@@ -743,12 +936,14 @@ def run_one(args, ws, rank, local):
                        "workspace_bytes": info.workspace_bytes, "est_ops": info.est_flop},
             "kernel_ms_per_call": {kk: v[1] / max(1, args.steps) for kk, v in kt.items()}}
     if info.method == 1 and "k_direct_fp8" in kt:
-        mp, src = _peaks()
-        peak = 2.0 * float(mp.get("bf16_tflops_sustained", mp.get("bf16_tflops")))
-        achieved = info.est_flop / (kt["k_direct_fp8"][1] / max(1, args.steps) * 1e-3) / 1e12
-        line["roofline"] = {"kernel": "k_direct_fp8", "bound": "tensor", "achieved": achieved, "peak": peak,
-                            "unit": "TFLOP/s", "frac": achieved / peak,
-                            "peak_source": f"{src} bf16 sustained x 2 (nominal fp8/bf16 dense ratio)"}
+        peak, _, _, src = _fp8_peak()
+        ksec = kt["k_direct_fp8"][1] / max(1, args.steps) * 1e-3
+        work = _method_flop(int(np.count_nonzero(se.mask)), L, n * n)
+        line["roofline"] = {"kernel": "k_direct_fp8", "bound": "tensor", "achieved": work / ksec / 1e12,
+                            "peak": peak, "unit": "TFLOP/s", "frac": work / ksec / 1e12 / peak,
+                            "planned_issued_frac": info.est_flop / ksec / 1e12 / peak,
+                            "work": "method: 2 |B| L FLOP per output pixel",
+                            "peak_source": f"{src} bf16 burst x 2 (nominal fp8/bf16 dense ratio)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

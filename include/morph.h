@@ -121,6 +121,11 @@ typedef struct {
     int unit_tiles;          /* direct route: horizontally adjacent tiles per work unit (1 or 2) */
     int unit_blocks;         /* direct route: 128-byte K blocks of image planes staged per SE row
                                 and unit (two tiles share them) */
+    int k_steps;             /* direct route: 32-column K steps per SE row and tile */
+    int level_chunks;        /* direct route: chunks of 16 grey levels a unit contracts when its
+                                band holds every level (est_flop counts that many); a unit's
+                                band usually needs fewer */
+    int ring_stages;         /* direct route: stages of the kernel's shared-memory operand ring */
 } morph_plan_info;
 
 /* --------------------------------------------------------------- calls */
@@ -142,7 +147,10 @@ int morph_ctx_set_cache_limit(morph_ctx *ctx, size_t bytes);
 int morph_ctx_cache_info(const morph_ctx *ctx, size_t *bytes, int *nplans);
 
 /* Plan (without running) the dilation (op = 0) or erosion (op = 1) of `f` by
- * `b` under `opts` (nullable = AUTO).  Host-only except for a device query. */
+ * `b` under `opts` (nullable = AUTO).  With a context the plan is built and
+ * cached (the direct route's SE blocks are written on the device); with
+ * ctx = NULL nothing touches the device and only the host-side figures are
+ * filled in. */
 int morph_plan_query(morph_ctx *ctx, const morph_image *f, const morph_se *b, int op,
                      const morph_opts *opts, morph_plan_info *out);
 
@@ -283,6 +291,23 @@ const char *morph_strerror(int status);
 /* Number of kernel launches the library issued through this context since
  * creation (every launch, every route). */
 uint64_t morph_launch_count(const morph_ctx *ctx);
+
+/* Limit, in nanoseconds, of every bounded device wait of the library's
+ * pipelined kernels launched through this context from now on (ns = 0: the
+ * default, 4 s).  A wait that reaches its limit makes its thread block stop:
+ * it raises the device error word, lets the copies and tensor-core work it
+ * already issued complete, frees its tensor memory and returns, so that
+ * morph_stream_check reports MORPH_E_TIMEOUT and the context stays usable.
+ * A failure-handling hook: a limit shorter than the kernel's ordinary waits
+ * (a few microseconds) makes that path run on purpose.  Host-only. */
+int morph_ctx_set_wait_limit(morph_ctx *ctx, uint64_t ns);
+
+/* Number of tcgen05 MMA instructions (M = 128, N = 256, K = 32, FP8; each
+ * 2 x 128 x 256 x 32 FLOP) that the FP8 direct route's kernel issued through
+ * this context since creation, counted on the device by the issuing thread
+ * (a measurement hook: the issued tensor work, zero-padding included).
+ * Synchronises the device; *out receives the count. */
+int morph_mma_count(morph_ctx *ctx, uint64_t *out);
 
 /* Per-kernel device time, summed over the launches recorded while profiling
  * was on. */

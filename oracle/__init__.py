@@ -19,6 +19,9 @@ Every function computes the plain definition from the paper:
   with a minus sign).
 * :func:`dilate3d` / :func:`erode3d` -- the definitions on 3-D volumes with a
   3-D SE (the method is stated for N-D images, Sec. 2.1 and Sec. 3).
+* :func:`opening` / :func:`closing` / :func:`gradient` -- the composite
+  operators named in the paper's conclusion, written out in NumPy on the raw
+  integer intermediate (no tonal shift).
 
 The arithmetic lives in ``morph_oracle.c`` (plain C, OpenMP over image rows
 only); :func:`build` compiles it with gcc.
@@ -227,3 +230,77 @@ def erode3d(f, L, mask, offset, origin, nthreads=1):
 def max_threads() -> int:
     """Threads an OpenMP region of the oracle would use."""
     return int(_load().orc_max_threads())
+
+
+# ---------------------------------------------------------------- composites
+# Opening, closing and the Beucher gradient (the combinations named in the
+# paper's conclusion), written out from the definitions of Sec. 2.1 on the raw
+# integer intermediate, with no tonal shift: the erosion's result may be
+# negative.  Empty-tap convention: where no tap is valid, a dilation gives the
+# lowest value of its input's tonal range and an erosion the highest (for an
+# image in [0, L) these are Eq. 6's 0 and L - 1).  The erosion result lies in
+# [-max b, L - 1] and the dilation result in [0, L - 1 + max b].
+
+def _dilate_raw(g, lo, mask, offset, origin):
+    """max over taps y in B with x - y in F of g(x - y) + b(y) (Eq. 6new); lo where none."""
+    g = np.asarray(g, np.int64)
+    N, H, W = g.shape
+    oy, ox = int(origin[0]), int(origin[1])
+    none = np.iinfo(np.int64).min
+    out = np.full(g.shape, none, np.int64)
+    for r, c in zip(*np.nonzero(np.asarray(mask))):
+        dy, dx = int(r) - oy, int(c) - ox                   # y = (dy, dx); source x - y
+        i0, i1 = max(0, dy), min(H, H + dy)
+        j0, j1 = max(0, dx), min(W, W + dx)
+        if i0 >= i1 or j0 >= j1:
+            continue
+        cand = g[:, i0 - dy:i1 - dy, j0 - dx:j1 - dx] + int(offset[r, c])
+        out[:, i0:i1, j0:j1] = np.maximum(out[:, i0:i1, j0:j1], cand)
+    out[out == none] = lo
+    return out
+
+
+def _erode_raw(g, hi, mask, offset, origin):
+    """min over taps y in B with x + y in F of g(x + y) - b(y) (Eq. Erosion); hi where none."""
+    g = np.asarray(g, np.int64)
+    N, H, W = g.shape
+    oy, ox = int(origin[0]), int(origin[1])
+    none = np.iinfo(np.int64).max
+    out = np.full(g.shape, none, np.int64)
+    for r, c in zip(*np.nonzero(np.asarray(mask))):
+        dy, dx = int(r) - oy, int(c) - ox                   # y = (dy, dx); source x + y
+        i0, i1 = max(0, -dy), min(H, H - dy)
+        j0, j1 = max(0, -dx), min(W, W - dx)
+        if i0 >= i1 or j0 >= j1:
+            continue
+        cand = g[:, i0 + dy:i1 + dy, j0 + dx:j1 + dx] - int(offset[r, c])
+        out[:, i0:i1, j0:j1] = np.minimum(out[:, i0:i1, j0:j1], cand)
+    out[out == none] = hi
+    return out
+
+
+def _prep3(f):
+    f = np.asarray(f)
+    return f[None] if f.ndim == 2 else f
+
+
+def opening(f, L, mask, offset, origin):
+    """(f erode b) dilate b on the raw integers; int64 [N, H, W]."""
+    f = _prep3(f)
+    mb = max_offset(mask, offset)
+    E = _erode_raw(f, int(L) - 1, mask, offset, origin)         # in [-max b, L - 1]
+    return _dilate_raw(E, -mb, mask, offset, origin)
+
+
+def closing(f, L, mask, offset, origin):
+    """(f dilate b) erode b on the raw integers; int64 [N, H, W]."""
+    f = _prep3(f)
+    mb = max_offset(mask, offset)
+    D = _dilate_raw(f, 0, mask, offset, origin)                 # in [0, L - 1 + max b]
+    return _erode_raw(D, int(L) - 1 + mb, mask, offset, origin)
+
+
+def gradient(f, L, mask, offset, origin):
+    """Beucher gradient (f dilate b) - (f erode b); int64 [N, H, W]."""
+    f = _prep3(f)
+    return _dilate_raw(f, 0, mask, offset, origin) - _erode_raw(f, int(L) - 1, mask, offset, origin)

@@ -21,12 +21,15 @@
 //             row x grey level, K = a window of image columns;
 //   D       : 128 x 256 FP32 accumulator in TMEM.
 // M = 128 stacks G offset groups x J = 128 / G output columns, N = 256
-// stacks rows_n image rows x Lpad levels.  The epilogue reads a lane per
-// (group, column), finds each group's top level by a descending scan and
-// combines groups with (max, sum-at-max).
+// stacks rows_n image rows x Lc grey levels (16 x 16 when L <= 16, else
+// 32 x 8).  A unit's levels are covered in chunks of Lc from the top of its
+// level band (see "level bands" below): Step 3 needs only the degrees at or
+// above each pixel's dilation value.  The epilogue reads a lane per (group,
+// column), finds each group's top level by a descending scan and combines
+// groups and chunks with (max, sum-at-max).
 //
 // Warp roles (192 threads, one persistent CTA per SM):
-//   warp 0   : TMA producer (one lane) -- A and B tiles into a 4-stage ring;
+//   warp 0   : TMA producer (one lane) -- A and B tiles into a 3-stage ring;
 //   warp 1   : TMEM allocator + MMA issuer (one lane), tcgen05.mma kind::f8f6f4;
 //   warps 2-5: epilogue (TMEM -> registers -> SMEM reduction -> int32 output).
 // Two TMEM accumulators (2 x 256 columns) let the epilogue of one unit
@@ -43,6 +46,8 @@
 // / 128) blocks for both tiles instead of nk per tile, the blocks past the
 // last A block carrying B only; each stage is released after the next
 // stage's MMAs.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cstring>
 
@@ -51,12 +56,13 @@
 
 namespace morph {
 
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr int kStageA = 128 * 128;             // 16 KB: 128 Toeplitz rows x 128 B of K
 constexpr int kStageB = kDirectN * 128;        // 32 KB: 256 (row, level) rows x 128 B of K
 constexpr int kStageBytes = kStageA + kStageB;
-constexpr int kRedEntries = 16 * 128;          // rows_n (<= 16) x 128 lanes
-constexpr int kRunEntries = 2048;              // rows_n x J  (= 256 / Lpad * 128 / G <= 2048)
+constexpr int kRedEntries = 32 * 128;          // rows_n (<= 32) x 128 lanes; with 16 rows, both tiles of a
+                                               // two-tile unit are read out before either is reduced
+constexpr int kRunEntries = 4096;              // rows_n x J x T (<= 4096: 32 x 128, or 16 x 128 x 2)
 constexpr int kDirectThreads = 192;
 constexpr uint32_t kTmemCols = 2 * kDirectN;   // two accumulators
 
@@ -100,6 +106,27 @@ __device__ __forceinline__ TileCoord direct_tile(const DirectProblemDev* P, long
     return c;
 }
 
+// The unit's level band (see DirectBand); without a band buffer every level
+// is covered.
+__device__ __forceinline__ DirectBand direct_band(const DirectProblemDev* P, long long t) {
+    if (P->band != nullptr) return P->band[t - P->tile_base];
+    DirectBand b;
+    b.hi = P->L - 1;
+    b.lb = -1;
+    return b;
+}
+
+// Chunks of Lc levels that pass p of the unit contracts (0: the pass cannot
+// reach the unit's lower bound and is skipped).
+__device__ __forceinline__ int direct_pass_chunks(const DirectProblemDev* P, const DirectBand& b, int p) {
+    const int* gw = P->meta + (P->n_pass + 1) + p * 8;
+    int wmax = 0;
+    for (int g = 0; g < P->G; ++g) wmax = max(wmax, gw[g]);
+    const int lo = b.lb - wmax;
+    if (lo > b.hi) return 0;
+    return (b.hi - max(lo, 0)) / P->Lc + 1;
+}
+
 __device__ __forceinline__ bool epi_any_failed(bool failed) {
     uint32_t any;
     asm volatile(
@@ -124,6 +151,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
     int2* run = red + kRedEntries;
     DirectSmemTail* tail = reinterpret_cast<DirectSmemTail*>(run + kRunEntries);
     volatile int* abort_flag = &tail->abort;
+    const unsigned long long wait_ns = dl.wait_ns != 0ull ? dl.wait_ns : kWaitLimitNs;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -163,31 +191,40 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 tma_fence_acquire_desc(&P->tmB);
             }
             const TileCoord tc = direct_tile(P, t);
+            const DirectBand bd = direct_band(P, t);
             const int* rb = P->meta;
             const int* rows = P->meta + (P->n_pass + 1) + P->n_pass * 8;
             const int xw = tc.j0 - (P->kw - 1) + P->ox + P->shift;   // plane column of the K window (32-aligned)
             const int y0 = tc.i0 + P->oy, nk = P->nk, nb = P->nb, n_pass = P->n_pass;
             for (int p = 0; ok && p < n_pass; ++p) {
+              const int nch = direct_pass_chunks(P, bd, p);
+              for (int ch = 0; ok && ch < nch; ++ch) {
+                // offset-group pass p, grey-level chunk ch (levels from `lev`, zero-filled by the copy
+                // where they fall outside 0..L-1)
+                const int lev = bd.hi - P->Lc * (ch + 1) + 1;
                 const int q_end = rb[p + 1];
                 for (int q = rb[p]; ok && q < q_end; ++q) {
                     const int y = y0 - rows[q];
                     for (int kc = 0; kc < nb; ++kc) {
                         const uint32_t s = it % kStages;
                         const uint32_t ph = (it / kStages) & 1u;
-                        if (!mbar_wait(empty0 + 8u * s, ph ^ 1u, abort_flag, dl.err)) { ok = false; break; }
+                        if (!mbar_wait(empty0 + 8u * s, ph ^ 1u, abort_flag, dl.err, wait_ns)) { ok = false; break; }
                         const uint32_t fb = full0 + 8u * s;
                         const bool with_a = kc < nk;   // split units stage one B block past the last A block
                         mbar_arrive_expect_tx(fb, with_a ? kStageBytes : kStageB);
                         const uint32_t sa = ring0 + s * kStageBytes;
                         if (with_a) tma_load_2d(sa, &P->tmA, 0, (q * nk + kc) * 128, fb);
-                        tma_load_4d(sa + kStageA, &P->tmB, xw + 128 * kc, 0, y, tc.n, fb);
+                        tma_load_4d(sa + kStageA, &P->tmB, xw + 128 * kc, lev, y, tc.n, fb);
                         ++it;
                     }
                 }
+              }
             }
         }
-        if (!ok) {
-            // drain: let the copies already issued land before the CTA exits
+        // drain, on every exit: the copies already issued land before the CTA may exit, also when
+        // another role gave up while this loop ran to its end (in the normal course they have
+        // landed already; older copies landed before their slot was refilled)
+        {
             const uint32_t nd = it < static_cast<uint32_t>(kStages) ? it : static_cast<uint32_t>(kStages);
             for (uint32_t d = 0; d < nd; ++d) {
                 const uint32_t k = it - 1 - d;
@@ -204,6 +241,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         uint32_t it = 0;
         uint32_t use0 = 0u, use1 = 0u;   // completed claims of TMEM accumulator slots 0 and 1
         uint32_t next_slot = 0;
+        unsigned long long n_mma = 0;    // MMAs this thread issued (measurement hook)
         bool ok = true;
         for (long long t = blockIdx.x; ok && t < dl.total_tiles; t += gridDim.x) {
             const DirectProblemDev* P = direct_find(dl, t);
@@ -213,14 +251,17 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
             const uint64_t boff1 = static_cast<uint64_t>(P->J) >> 4;   // second tile: J bytes further along K
             const int sh1 = P->J >> 5;                                  // the same shift in 32-byte K steps
             const int ksteps = P->ksteps, nk = P->nk, nb = P->nb;
+            const DirectBand bd = direct_band(P, t);
             for (int p = 0; ok && p < P->n_pass; ++p) {
+              const int nch = direct_pass_chunks(P, bd, p);
+              for (int ch = 0; ok && ch < nch; ++ch) {
                 // a unit claims one slot (T = 1, alternating) or both (T = 2)
                 const uint32_t s0 = two ? 0u : next_slot;
                 next_slot = two ? 0u : (next_slot ^ 1u);
                 if (two || s0 == 0u)
-                    ok = mbar_wait(smem_u32(&tail->tempty[0]), (use0 & 1u) ^ 1u, abort_flag, dl.err);
+                    ok = mbar_wait(smem_u32(&tail->tempty[0]), (use0 & 1u) ^ 1u, abort_flag, dl.err, wait_ns);
                 if (ok && (two || s0 == 1u))
-                    ok = mbar_wait(smem_u32(&tail->tempty[1]), (use1 & 1u) ^ 1u, abort_flag, dl.err);
+                    ok = mbar_wait(smem_u32(&tail->tempty[1]), (use1 & 1u) ^ 1u, abort_flag, dl.err, wait_ns);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + s0 * kDirectN;
@@ -231,7 +272,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                     for (int kc = 0; kc < nb; ++kc) {
                         const uint32_t s = it % kStages;
                         const uint32_t ph = (it / kStages) & 1u;
-                        if (!mbar_wait(full0 + 8u * s, ph, abort_flag, dl.err)) { ok = false; break; }
+                        if (!mbar_wait(full0 + 8u * s, ph, abort_flag, dl.err, wait_ns)) { ok = false; break; }
                         tc_fence_after();
                         const uint64_t adesc = desc0 + static_cast<uint64_t>(s * (kStageBytes >> 4));
                         const uint64_t bdesc = adesc + static_cast<uint64_t>(kStageA >> 4);
@@ -242,6 +283,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                             const uint64_t adesc_prev = desc0 + static_cast<uint64_t>(s_prev * (kStageBytes >> 4));
                             {
                                 const int lo = 4 * kc, hi = min(ksteps, 4 * kc + 4);
+                                n_mma += static_cast<unsigned long long>(max(0, hi - lo));
                                 for (int ks = lo; ks < hi; ++ks) {
                                     tc_mma_f8(d_tmem, adesc + 2ull * (ks & 3), bdesc + 2ull * (ks & 3), idesc, acc);
                                     acc = 1;
@@ -249,6 +291,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                             }
                             {
                                 const int lo = max(0, 4 * kc - sh1), hi = min(ksteps, 4 * kc + 4 - sh1);
+                                n_mma += static_cast<unsigned long long>(max(0, hi - lo));
                                 for (int ks = lo; ks < hi; ++ks) {
                                     const uint64_t ad = ((ks >> 2) == kc ? adesc : adesc_prev) + 2ull * (ks & 3);
                                     tc_mma_f8(d_tmem + kDirectN, ad, bdesc + 2ull * ((ks + sh1) & 3), idesc, acc1);
@@ -263,6 +306,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                             continue;
                         }
                         const int nks = min(4, ksteps - 4 * kc);
+                        n_mma += static_cast<unsigned long long>(two ? 2 * nks : nks);
                         // advance the start addresses by 32 B of K inside the 128-B swizzled rows
                         if (two) {
                             for (int ks = 0; ks < nks; ++ks) {
@@ -287,12 +331,14 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 }
                 if (two || s0 == 0u) ++use0;
                 if (two || s0 == 1u) ++use1;
+              }
             }
         }
-        if (!ok) {
-            tc_commit(smem_u32(&tail->drain));
-            mbar_wait_drain(smem_u32(&tail->drain), 0);
-        }
+        // drain, on every exit: every issued MMA completes before TMEM is freed, also when the
+        // epilogue gave up and no longer waits for the accumulators
+        tc_commit(smem_u32(&tail->drain));
+        mbar_wait_drain(smem_u32(&tail->drain), 0);
+        if (dl.mma_count != nullptr && n_mma != 0) atomicAdd(dl.mma_count, n_mma);
     } else if (warp >= 2) {
         // ----------------------------------------------------------- epilogue
         const int quarter = warp & 3;                 // TMEM lane quarter this warp may access
@@ -303,21 +349,31 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         for (long long t = blockIdx.x; t < dl.total_tiles; t += gridDim.x) {
             const DirectProblemDev* P = direct_find(dl, t);
             const TileCoord tc = direct_tile(P, t);
-            const int J = P->J, G = P->G, rows_n = P->rows_n, Lpad = P->Lpad, T = (TT == 0) ? P->T : (TT == 3 ? 2 : TT);
+            const int J = P->J, G = P->G, rows_n = P->rows_n, Lc = P->Lc, T = (TT == 0) ? P->T : (TT == 3 ? 2 : TT);
             const int g = m / J;
             const int* gw = P->meta + (P->n_pass + 1);
+            const DirectBand bd = direct_band(P, t);
+            int n_units = 0;                              // accumulations of this unit, all passes
+            for (int p = 0; p < P->n_pass; ++p) n_units += direct_pass_chunks(P, bd, p);
             bool failed = false;
-            for (int p = 0; p < P->n_pass; ++p) {
+            int p = 0, ch = 0, nch = direct_pass_chunks(P, bd, 0);
+            for (int u = 0; u < n_units; ++u, ++ch) {
+                while (ch >= nch) {                       // next pass with chunks
+                    ++p;
+                    ch = 0;
+                    nch = direct_pass_chunks(P, bd, p);
+                }
+                const int lev0 = bd.hi - Lc * (ch + 1) + 1;   // grey level of this chunk's first column
                 const uint32_t s0 = (T == 2) ? 0u : next_slot;
                 next_slot = (T == 2) ? 0u : (next_slot ^ 1u);
                 bool ok = true;
-                if (T == 2 || s0 == 0u) ok = mbar_wait(smem_u32(&tail->tfull[0]), use0 & 1u, abort_flag, dl.err);
+                if (T == 2 || s0 == 0u) ok = mbar_wait(smem_u32(&tail->tfull[0]), use0 & 1u, abort_flag, dl.err, wait_ns);
                 if (ok && (T == 2 || s0 == 1u))
-                    ok = mbar_wait(smem_u32(&tail->tfull[1]), use1 & 1u, abort_flag, dl.err);
+                    ok = mbar_wait(smem_u32(&tail->tfull[1]), use1 & 1u, abort_flag, dl.err, wait_ns);
                 if (epi_any_failed(!ok)) { failed = true; break; }
                 tc_fence_after();
-                const int wg = (g < G) ? gw[p * 8 + g] : 0;
-                // (max, sum-at-max) over the groups of tile tt, merged with the earlier passes
+                const int wg = ((g < G) ? gw[p * 8 + g] : 0) + lev0;   // degree of the chunk's level 0 in group g
+                // (max, sum-at-max) over the groups of tile tt, merged with the earlier unit passes
                 const int pairs = rows_n * J;
                 auto reduce = [&](int tt, int rbase) {
                     for (int idx = et; idx < pairs; idx += 128) {
@@ -330,18 +386,19 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                         }
                         int2 cur = make_int2(best, bc);
                         const int ri = tt * pairs + idx;
-                        if (p > 0) {
+                        if (u > 0) {
                             const int2 prev = run[ri];
                             if (prev.x > cur.x) cur = prev;
                             else if (prev.x == cur.x && cur.x >= 0) cur.y += prev.y;
                         }
                         run[ri] = cur;
-                        if (p == P->n_pass - 1) {
+                        if (u == n_units - 1) {
                             const int i = tc.i0 + tr, j = tc.j0 + tt * J + jl;
                             if (i < P->h && j >= 0 && j < P->w) {
                                 const int dval = cur.x < 0 ? 0 : cur.x;
                                 const long long o = (static_cast<long long>(tc.n) * P->h + i) * P->w + j;
-                                P->out[o] = P->erode ? (P->L - 1 - dval) : dval;
+                                P->out[o] = (P->erode ? (P->L - 1 - dval) : dval) + P->out_add -
+                                            (P->out_sub ? P->out_sub[o] : 0);
                                 if (P->out_cnt) P->out_cnt[o] = cur.x < 0 ? 0 : cur.y;
                             }
                         }
@@ -355,10 +412,17 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                     const uint32_t trow =
                         tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + (s0 + tt) * kDirectN;
                     for (int tr = 0; tr < rows_n; ++tr) {
-                        const uint32_t col0 = static_cast<uint32_t>(tr * Lpad);
+                        const uint32_t col0 = static_cast<uint32_t>(tr * Lc);
                         int top = -1;
                         float cnt = 0.f;
-                        if (Lpad == 16) {
+                        if (Lc == 8) {
+                            float v[8];
+                            tmem_ld_32x32b_x8(trow + col0, v);
+                            tc_wait_ld();
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)
+                                if (v[k] > 0.5f) { top = k; cnt = v[k]; }
+                        } else if (Lc == 16) {
                             float v[16];
                             tmem_ld_32x32b_x16(trow + col0, v);
                             tc_wait_ld();
@@ -366,7 +430,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                             for (int k = 0; k < 16; ++k)
                                 if (v[k] > 0.5f) { top = k; cnt = v[k]; }
                         } else {
-                            for (int c = Lpad / 32 - 1; c >= 0; --c) {
+                            for (int c = Lc / 32 - 1; c >= 0; --c) {
                                 if (__all_sync(0xffffffffu, top >= 0)) break;
                                 float v[32];
                                 tmem_ld_32x32b_x32(trow + col0 + 32u * c, v);
@@ -417,9 +481,19 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
 // blocks[(q * nk + kc)][m][k] = 1.0 (E4M3) iff the tap (r_q, c) with
 // c = j + (kw - 1) - (128 kc + k), j = m mod J, lies in B and its offset is
 // the level of group g = m / J of the pass that owns row index q.
+// reflect: the offsets are in the original (unreflected) box order, read at
+// kh kw - 1 - t (the erosion of a device-resident SE); err != nullptr: an
+// offset of a tap outside [0, bound] is reported as a data error (the
+// device-resident SE's declared bound).
 __global__ void k_build_toeplitz(uint8_t* __restrict__ blocks, long long nbytes, const uint8_t* __restrict__ mask,
                                  const int* __restrict__ off, const int* __restrict__ meta, int n_pass, int nk, int J,
-                                 int G, int kw) {
+                                 int G, int kw, int nbox, int reflect, int bound, unsigned int* __restrict__ err) {
+    if (err != nullptr) {
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nbox; t += (long long)gridDim.x * blockDim.x) {
+            const int o = off[t];
+            if (mask[reflect ? nbox - 1 - t : t] && (o < 0 || o > bound)) atomicOr(err, MORPH_DEVERR_RANGE);
+        }
+    }
     const int* rb = meta;
     const int* gw = meta + (n_pass + 1);
     const int* rows = gw + n_pass * 8;
@@ -438,7 +512,7 @@ __global__ void k_build_toeplitz(uint8_t* __restrict__ blocks, long long nbytes,
         uint8_t v = 0;
         if (g < G && c >= 0 && c < kw) {
             const int t = r * kw + c;
-            if (mask[t] && off[t] == gw[p * 8 + g]) v = 0x38;
+            if (mask[t] && off[reflect ? nbox - 1 - t : t] == gw[p * 8 + g]) v = 0x38;
         }
         blocks[idx] = v;
     }
@@ -450,12 +524,18 @@ DirectPlan::~DirectPlan() {
 }
 
 // Host part of the plan: tiles, groups, passes, metadata and the issued FLOP.
-int plan_direct_host(const morph_image* f, const morph_se* se, int erode, DirectPlan* p) {
+int plan_direct_host(const morph_image* f, const morph_se* se, int erode, DirectPlan* p, int dev_bound) {
+    // dev_bound >= 0: the offsets are in device memory (se->offset is not read); every level
+    // 0..dev_bound is planned for, every SE row with a tap takes part in every pass, and the
+    // band taps carry the tap's box index, -(t + 1), for the band kernel to look the offset up
+    const bool dev = dev_bound >= 0;
     const int kh = se->kh, kw = se->kw;
     p->L = f->L;
-    p->Lpad = 16;
-    while (p->Lpad < f->L) p->Lpad <<= 1;
-    p->rows_n = kDirectN / p->Lpad;
+    // N = rows_n image rows x Lc levels: one 16-level chunk holds every level up to L = 16; above
+    // that a unit's level band usually spans few levels, and 8-level chunks of 32-row units
+    // contract about half as many levels as 16-level ones
+    p->Lc = f->L > kDirectLc ? kDirectLcBand : kDirectLc;
+    p->rows_n = kDirectN / p->Lc;
     p->kh = kh;
     p->kw = kw;
     p->oy = se->oy;
@@ -473,8 +553,13 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     for (int t = 0; t < kh * kw; ++t) {
         if (!se->mask[t]) continue;
         ++taps;
+        if (dev) continue;
         maxb = std::max(maxb, static_cast<int>(se->offset[t]));
         levels.push_back(se->offset[t]);
+    }
+    if (dev) {
+        maxb = dev_bound;
+        for (int v = 0; v <= dev_bound; ++v) levels.push_back(v);
     }
     std::sort(levels.begin(), levels.end());
     levels.erase(std::unique(levels.begin(), levels.end()), levels.end());
@@ -538,6 +623,7 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
             for (int c = 0; c < kw && !any; ++c) {
                 const int t = r * kw + c;
                 if (!se->mask[t]) continue;
+                if (dev) { any = true; break; }
                 for (int g = 0; g < p->G; ++g)
                     if (gw[ps * 8 + g] == se->offset[t]) { any = true; break; }
             }
@@ -551,9 +637,47 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     p->meta.insert(p->meta.end(), rb.begin(), rb.end());
     p->meta.insert(p->meta.end(), gw.begin(), gw.end());
     p->meta.insert(p->meta.end(), rows.begin(), rows.end());
+    // taps of the per-unit lower bound on the top degree: the SE box cut into up to 16 x 16
+    // cells, from each the tap with the largest offset (ties: nearest the cell centre), plus
+    // the origin when it is a tap (valid at every pixel of the image); stored as the source
+    // displacement (oy - r, ox - c) and b
+    p->band_tap_off = static_cast<int>(p->meta.size());
+    {
+        const int ny = std::min(16, kh), nx = std::min(16, kw);
+        std::vector<int> bt;
+        bool has_origin = false;
+        for (int a = 0; a < ny; ++a)
+            for (int b2 = 0; b2 < nx; ++b2) {
+                const int r0 = a * kh / ny, r1 = (a + 1) * kh / ny, c0 = b2 * kw / nx, c1 = (b2 + 1) * kw / nx;
+                int best_t = -1;
+                long long best_key = 0;
+                for (int r = r0; r < r1; ++r)
+                    for (int c = c0; c < c1; ++c) {
+                        const int t = r * kw + c;
+                        if (!se->mask[t]) continue;
+                        const long long dr = 2 * r - (r0 + r1 - 1), dc = 2 * c - (c0 + c1 - 1);
+                        const long long key = (dev ? 0LL : static_cast<long long>(se->offset[t]) * (1LL << 40)) -
+                                              (dr * dr + dc * dc);
+                        if (best_t < 0 || key > best_key) {
+                            best_t = t;
+                            best_key = key;
+                        }
+                    }
+                if (best_t < 0) continue;
+                const int r = best_t / kw, c = best_t % kw;
+                if (r == se->oy && c == se->ox) has_origin = true;
+                bt.insert(bt.end(), {se->oy - r, se->ox - c, dev ? -(best_t + 1) : static_cast<int>(se->offset[best_t])});
+            }
+        if (!has_origin && se->oy >= 0 && se->oy < kh && se->ox >= 0 && se->ox < kw && se->mask[se->oy * kw + se->ox]) {
+            const int t0 = se->oy * kw + se->ox;
+            bt.insert(bt.end(), {0, 0, dev ? -(t0 + 1) : static_cast<int>(se->offset[t0])});
+        }
+        p->n_band_taps = static_cast<int>(bt.size() / 3);
+        p->meta.insert(p->meta.end(), bt.begin(), bt.end());
+    }
     p->toeplitz_blocks = p->active_rows_total * p->nk;
     p->issued_flop = static_cast<double>(p->tiles) * p->T * static_cast<double>(p->active_rows_total) * p->ksteps * 2.0 *
-                     kDirectM * kDirectN * 32.0;
+                     kDirectM * kDirectN * 32.0 * ((p->L + p->Lc - 1) / p->Lc);
 
     return MORPH_OK;
 }
@@ -583,7 +707,8 @@ int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, 
         long long blocks = (static_cast<long long>(tb) + 255) / 256;
         if (blocks > 4096) blocks = 4096;
         k_build_toeplitz<<<static_cast<unsigned>(blocks), 256>>>(p->d_toeplitz, static_cast<long long>(tb), d_mask,
-                                                                d_off, p->d_meta, p->n_pass, p->nk, p->J, p->G, kw);
+                                                                d_off, p->d_meta, p->n_pass, p->nk, p->J, p->G, kw,
+                                                                kh * kw, 0, 0, nullptr);
         ctx->launches += 1;
         MORPH_CUDA_TRY(cudaGetLastError());
         MORPH_CUDA_TRY(cudaDeviceSynchronize());
@@ -606,17 +731,24 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
                               static_cast<uint64_t>(p.nimg)};
     const uint64_t strides[3] = {static_cast<uint64_t>(p.w_pad), static_cast<uint64_t>(p.w_pad) * p.L,
                                  static_cast<uint64_t>(p.w_pad) * p.L * p.h};
-    const uint32_t box[4] = {128, static_cast<uint32_t>(p.Lpad), static_cast<uint32_t>(p.rows_n), 1};
+    const uint32_t box[4] = {128, static_cast<uint32_t>(p.Lc), static_cast<uint32_t>(p.rows_n), 1};
     *status = encode_tmap(&d->tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, const_cast<uint8_t*>(planes), dims, strides, box,
                           CU_TENSOR_MAP_SWIZZLE_128B);
     d->out = out;
     d->out_cnt = out_cnt;
+    d->out_add = 0;
+    d->out_sub = nullptr;
     d->meta = p.d_meta;
     d->h = p.h;
     d->w = p.w;
     d->nimg = p.nimg;
     d->L = p.L;
-    d->Lpad = p.Lpad;
+    d->Lc = p.Lc;
+    d->maxb = p.maxb;
+    d->kh = p.kh;
+    d->band_tap_off = p.band_tap_off;
+    d->n_band_taps = p.n_band_taps;
+    d->band = nullptr;
     d->rows_n = p.rows_n;
     d->J = p.J;
     d->G = p.G;
@@ -639,6 +771,233 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
 }
 
 int direct_kind(const DirectProblemDev& d) { return d.split ? 3 : d.T; }
+
+void direct_fill_band(DirectProblemDev* d, const morph_image* f, DirectBand* band) {
+    // with L <= Lc one chunk holds every level: no band to compute
+    d->band = f->L > d->Lc ? band : nullptr;
+    d->src = f->data;
+    d->dtype = f->dtype;
+    d->row_stride = f->row_stride;
+    d->batch_stride = f->batch_stride;
+}
+
+size_t direct_band_bytes(const morph_image* f) {
+    // units are rows_n >= 16 image rows by at least 16 columns
+    const size_t units = static_cast<size_t>(f->n) * ((f->h + 15) / 16) * ((f->w + 15) / 16);
+    return (units * sizeof(DirectBand) + 255) & ~size_t(255);
+}
+
+// ------------------------------------------------------------ level bands
+// Step 3 reads only the top nonzero degree D(x) of each pixel's count
+// polynomial and its coefficient; every product f(x - y) + b(y) that reaches
+// D(x) has f(x - y) >= D(x) - max b.  For a unit (rows_n x T J output pixels)
+// the kernel below computes
+//   hi = the largest level in the unit's input window (no tap reads a higher one),
+//   lb = min over the unit's pixels x of max over a subset S of the taps valid
+//        at x of level(f(x - y)) + b(y)     (<= D(x): a max over fewer taps),
+// so the levels that can hold any top degree of the unit lie in
+// [max(0, lb - max b), hi]; the direct kernel then contracts only those
+// levels (chunks of Lc from the top), and the coefficients it computes are
+// exactly those of the full polynomial at every degree >= lb.  A pixel with no
+// valid tap of S makes lb = -1, i.e. every level from 0.
+__device__ __forceinline__ int band_pixel(const void* src, int dtype, long long idx) {
+    if (dtype == MORPH_U8) return static_cast<const uint8_t*>(src)[idx];
+    if (dtype == MORPH_U16) return static_cast<const uint16_t*>(src)[idx];
+    return static_cast<const int32_t*>(src)[idx];
+}
+
+constexpr int kBandWinBytes = 96 * 1024;   // shared-memory window of a unit, 4 B per position
+constexpr int kBandPairs = 8;              // pixel pairs per thread (32 rows x 128 columns / 2 / 256 threads)
+constexpr int kBandWMax = 1024;            // offsets above this are lowered to it for the bound (fp16-exact sums)
+
+// Level of pixel (i, j), flipped for the erosion and clamped into [0, L).
+__device__ __forceinline__ int band_level(const DirectProblemDev* P, long long ibase, int i, int j) {
+    int v = band_pixel(P->src, P->dtype, ibase + static_cast<long long>(i) * P->row_stride + j);
+    v = min(max(v, 0), P->L - 1);          // out-of-range values are reported by the encoder
+    return P->erode ? P->L - 1 - v : v;
+}
+
+// Warp `warp` stages window rows rr = warp, warp + nwarp, ...: its (row, 32-column
+// group) items are taken eight at a time, so each lane has eight loads in flight
+// before it stores their levels (the staging is bound by load latency otherwise).
+template <typename Pix>
+__device__ __forceinline__ int band_stage_rows(const DirectProblemDev* P, long long ibase, int wr0, int wc0, int WR,
+                                               int WC, __half* qh, int warp, int nwarp, int lane) {
+    const Pix* src = static_cast<const Pix*>(P->src);
+    const int h = P->h, w = P->w, L = P->L, flip = P->erode;
+    const int ng = (WC + 31) >> 5;                                 // 32-column groups per row
+    const int my_rows = warp < WR ? (WR - warp + nwarp - 1) / nwarp : 0;
+    const int items = my_rows * ng;
+    int hi = -1;
+    for (int base = 0; base < items; base += 8) {
+        int v[8], rr[8], cc[8];
+        bool in[8];
+        int r = base / ng, gcol = base - r * ng;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            rr[k] = warp + r * nwarp;
+            cc[k] = gcol * 32 + lane;
+            const int i = wr0 + rr[k], j = wc0 + cc[k];
+            in[k] = base + k < items && cc[k] < WC && i >= 0 && i < h && j >= 0 && j < w;
+            v[k] = in[k] ? static_cast<int>(src[ibase + static_cast<long long>(i) * P->row_stride + j]) : 0;
+            if (++gcol == ng) {
+                gcol = 0;
+                ++r;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (base + k >= items || cc[k] >= WC) continue;
+            float fv = -4096.f;
+            if (in[k]) {
+                int lv = min(max(v[k], 0), L - 1);    // out-of-range values are reported by the encoder
+                lv = flip ? L - 1 - lv : lv;
+                hi = max(hi, lv);
+                fv = static_cast<float>(lv);
+            }
+            const __half hv = __float2half_rn(fv);
+            const int e = rr[k] * WC + cc[k];
+            qh[2 * e] = hv;                                        // low half of pair cc
+            if (cc[k] > 0) qh[2 * e - 1] = hv;                     // high half of pair cc - 1
+            if (cc[k] == WC - 1) qh[2 * e + 1] = __float2half_rn(-4096.f);   // the row's last pair
+        }
+    }
+    return hi;
+}
+
+__global__ void __launch_bounds__(256) k_band(const __grid_constant__ DirectLaunch dl) {
+    // The unit's input window (rows i - r + oy, columns j - c + ox over the SE box, not
+    // clipped) as overlapping half2 pairs q[r][k] = (level(r, k), level(r, k + 1)), -4096
+    // outside the image; a pixel pair (j, j + 1) reads a tap's two sources with one load.
+    // Sums level + min(b, 1024) <= 1279 and the sentinel -4096 + 1024 are exact in fp16.
+    extern __shared__ __align__(16) uint8_t s_raw[];
+    __half* qh = reinterpret_cast<__half*>(s_raw);
+    const __half2* q = reinterpret_cast<const __half2*>(s_raw);
+    __shared__ int s_hi[8], s_lb[8];
+    __shared__ int s_toff[kBandTapsMax];
+    __shared__ __half2 s_tw[kBandTapsMax];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (long long t = blockIdx.x; t < dl.total_tiles; t += gridDim.x) {
+        const DirectProblemDev* P = direct_find(dl, t);
+        if (P->band == nullptr) continue;             // every level (block-uniform branch)
+        const TileCoord tc = direct_tile(P, t);
+        const int h = P->h, w = P->w, uw = P->T * P->J, ntap = min(P->n_band_taps, kBandTapsMax);
+        const long long ibase = static_cast<long long>(tc.n) * P->batch_stride;
+        const int wr0 = tc.i0 - (P->kh - 1 - P->oy), wc0 = tc.j0 - (P->kw - 1 - P->ox);
+        const int WR = P->rows_n + P->kh - 1, WC = uw + P->kw;   // one spare column for the pairs
+        const bool fast = static_cast<long long>(WR) * WC * 4 <= kBandWinBytes &&
+                          P->rows_n * (uw >> 1) <= 256 * kBandPairs;      // block-uniform
+        __syncthreads();   // the previous unit's readers of the shared arrays are done
+        for (int k = threadIdx.x; k < ntap; k += blockDim.x) {
+            const int* tp = P->meta + P->band_tap_off + 3 * k;
+            s_toff[k] = tp[0] * WC + tp[1];
+            const float wv = static_cast<float>(min(tp[2], kBandWMax));
+            s_tw[k] = __floats2half2_rn(wv, wv);
+        }
+        int hi = -1;
+        int lb = 0x7fffffff;
+        if (fast) {
+            if (P->dtype == MORPH_U8)
+                hi = band_stage_rows<uint8_t>(P, ibase, wr0, wc0, WR, WC, qh, warp, nwarp, lane);
+            else if (P->dtype == MORPH_U16)
+                hi = band_stage_rows<uint16_t>(P, ibase, wr0, wc0, WR, WC, qh, warp, nwarp, lane);
+            else
+                hi = band_stage_rows<int32_t>(P, ibase, wr0, wc0, WR, WC, qh, warp, nwarp, lane);
+            __syncthreads();
+            // pixel pairs of the unit: rows_n rows x uw / 2 pairs per row, kBandPairs per thread
+            const int half_w = uw >> 1, sh = __ffs(half_w) - 1;
+            const int npair = P->rows_n * half_w;
+            __half2 acc[kBandPairs];
+            int base[kBandPairs];
+#pragma unroll
+            for (int k = 0; k < kBandPairs; ++k) {
+                acc[k] = __floats2half2_rn(-1.f, -1.f);
+                const int pp = threadIdx.x + k * 256;
+                const int pr = pp >> sh, pc = 2 * (pp & (half_w - 1));
+                base[k] = (pr + P->kh - 1 - P->oy) * WC + pc + P->kw - 1 - P->ox;
+            }
+            for (int s = 0; s < ntap; ++s) {
+                const int off = s_toff[s];
+                const __half2 tw = s_tw[s];
+#pragma unroll
+                for (int k = 0; k < kBandPairs; ++k)
+                    if (threadIdx.x + k * 256 < npair) acc[k] = __hmax2(acc[k], __hadd2(q[base[k] + off], tw));
+            }
+#pragma unroll
+            for (int k = 0; k < kBandPairs; ++k) {
+                const int pp = threadIdx.x + k * 256;
+                if (pp >= npair) continue;
+                const int i = tc.i0 + (pp >> sh), j = tc.j0 + 2 * (pp & (half_w - 1));
+                if (i >= h) continue;
+                const float2 m = __half22float2(acc[k]);
+                if (j >= 0 && j < w) lb = min(lb, static_cast<int>(m.x));
+                if (j + 1 >= 0 && j + 1 < w) lb = min(lb, static_cast<int>(m.y));
+            }
+        } else {
+            // windows too large for shared memory (SE boxes of hundreds of rows): direct loads
+            const int r0 = max(0, wr0), r1 = min(h, tc.i0 + P->rows_n + P->oy);
+            const int c0 = max(0, wc0), c1 = min(w, tc.j0 + uw + P->ox);
+            for (int i = r0 + warp; i < r1; i += nwarp)
+                for (int j = c0 + lane; j < c1; j += 32) hi = max(hi, band_level(P, ibase, i, j));
+            __syncthreads();
+            const int pi0 = max(0, tc.i0), pi1 = min(h, tc.i0 + P->rows_n);
+            const int pj0 = max(0, tc.j0), pj1 = min(w, tc.j0 + uw);
+            for (int i = pi0 + warp; i < pi1; i += nwarp)
+                for (int j = pj0 + lane; j < pj1; j += 32) {
+                    int m = -1;
+                    for (int s = 0; s < ntap; ++s) {
+                        const int* tp = P->meta + P->band_tap_off + 3 * s;
+                        const int si = i + tp[0], sj = j + tp[1];
+                        if (static_cast<unsigned>(si) < static_cast<unsigned>(h) &&
+                            static_cast<unsigned>(sj) < static_cast<unsigned>(w))
+                            m = max(m, band_level(P, ibase, si, sj) + min(tp[2], kBandWMax));
+                    }
+                    lb = min(lb, m);
+                }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            lb = min(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+        }
+        if (lane == 0) {
+            s_hi[warp] = hi;
+            s_lb[warp] = lb;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < nwarp; ++k) {
+                hi = max(hi, s_hi[k]);
+                lb = min(lb, s_lb[k]);
+            }
+            DirectBand b;
+            b.hi = hi < 0 ? P->L - 1 : hi;            // no pixel read: the unit's pixels have no valid tap
+            // lb <= D(x) <= hi + max b for every pixel with a valid tap, so the pass holding the
+            // largest offset always has a chunk; the clamp keeps that true for any input
+            b.lb = min(lb, b.hi + P->maxb);
+            const_cast<DirectBand*>(P->band)[t - P->tile_base] = b;
+        }
+    }
+}
+
+int launch_band(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st) {
+    if (dl.total_tiles <= 0) return MORPH_OK;
+    bool any = dl.many != nullptr || dl.single.band != nullptr;
+    if (!any) return MORPH_OK;
+    long long grid = dl.total_tiles;
+    const long long cap = static_cast<long long>(ctx->num_sms) * 2;   // 96 KB of shared memory each
+    if (grid > cap) grid = cap;
+    prof_begin(ctx, st, "k_band");
+    if (!kernels_ready(ctx->device, kGroupBand)) {
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandWinBytes));
+        mark_kernels_ready(ctx->device, kGroupBand);
+    }
+    k_band<<<static_cast<unsigned>(grid), 256, kBandWinBytes, st>>>(dl);
+    prof_end(ctx, st);
+    ctx->launches += 1;
+    MORPH_CUDA_TRY(cudaGetLastError());
+    return MORPH_OK;
+}
 
 int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_kind) {
     if (dl.total_tiles <= 0) return MORPH_OK;

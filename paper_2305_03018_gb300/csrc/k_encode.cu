@@ -96,19 +96,21 @@ int launch_encode(morph_ctx* ctx, const EncodeJob* jobs, int njobs, long long to
 
 // Output fill for a problem whose SE has no tap: Eq. 6 gives 0 for dilation,
 // the erosion convention gives L-1; the top count is 0.
-__global__ void k_fill_empty(int32_t* out, int32_t* cnt, long long n, int value) {
+__global__ void k_fill_empty(int32_t* out, int32_t* cnt, long long n, int value, const int32_t* sub) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        out[k] = value;
+        out[k] = value - (sub ? sub[k] : 0);
         if (cnt) cnt[k] = 0;
     }
 }
 
-int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st) {
+int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st,
+                      const OutAdjust* adj) {
     if (n <= 0) return MORPH_OK;
     long long blocks = (n + 255) / 256;
     if (blocks > ctx->num_sms * 8LL) blocks = ctx->num_sms * 8LL;
     prof_begin(ctx, st, "k_fill_empty");
-    k_fill_empty<<<static_cast<unsigned>(blocks), 256, 0, st>>>(out, cnt, n, value);
+    k_fill_empty<<<static_cast<unsigned>(blocks), 256, 0, st>>>(out, cnt, n, value + (adj ? adj->add : 0),
+                                                                adj ? adj->sub : nullptr);
     prof_end(ctx, st);
     ctx->launches += 1;
     MORPH_CUDA_TRY(cudaGetLastError());

@@ -204,6 +204,8 @@ struct FftArgs {
     void* buf;                // [wave_tiles][K][Ny][Nx]
     int32_t* out;
     int32_t* out_cnt;
+    int out_add;              // output adjustment of a composite's pass (OutAdjust)
+    const int32_t* out_sub;
     float* count_err;
     int validate;
     unsigned int* err;
@@ -413,7 +415,7 @@ __global__ void __launch_bounds__(256) k_fft_scan(const FftArgs a) {
         }
         const int dval = D < 0 ? 0 : D;
         const long long o = (static_cast<long long>(n) * a.h + i) * a.w + j;
-        a.out[o] = a.erode ? (a.L - 1 - dval) : dval;
+        a.out[o] = (a.erode ? (a.L - 1 - dval) : dval) + a.out_add - (a.out_sub ? a.out_sub[o] : 0);
         if (a.out_cnt) a.out_cnt[o] = D < 0 ? 0 : cnt;
     }
     if (a.count_err) {
@@ -485,7 +487,7 @@ __global__ void __launch_bounds__(512) k_fft_range(const FftArgs a) {
         if (lane == 0) {
             const int dval = D < 0 ? 0 : D;
             const long long o = (static_cast<long long>(n) * a.h + i) * a.w + j;
-            a.out[o] = a.erode ? (a.L - 1 - dval) : dval;
+            a.out[o] = (a.erode ? (a.L - 1 - dval) : dval) + a.out_add - (a.out_sub ? a.out_sub[o] : 0);
             if (a.out_cnt) a.out_cnt[o] = D < 0 ? 0 : cnt;
         }
     }
@@ -906,7 +908,8 @@ int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int
 
 template <typename T>
 static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out,
-                        int32_t* cnt, float* count_err, int validate, void* buf, cudaStream_t st) {
+                        int32_t* cnt, float* count_err, int validate, void* buf, cudaStream_t st,
+                        const OutAdjust* adj) {
     FftArgs a;
     std::memset(&a, 0, sizeof(a));
     a.src = f->data;
@@ -943,6 +946,8 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
     a.buf = buf;
     a.out = out;
     a.out_cnt = cnt;
+    a.out_add = adj ? adj->add : 0;
+    a.out_sub = adj ? adj->sub : nullptr;
     a.count_err = count_err;
     a.validate = validate;
     a.err = ctx->d_err;
@@ -982,18 +987,18 @@ static int launch_fft_t(morph_ctx* ctx, const FftPlan& p, const morph_image* f, 
 }
 
 int launch_fft_in(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-                  float* count_err, int validate, void* buf, cudaStream_t st) {
-    if (p.prec == 4) return launch_fft_t<float>(ctx, p, f, erode, out, cnt, count_err, validate, buf, st);
-    return launch_fft_t<double>(ctx, p, f, erode, out, cnt, count_err, validate, buf, st);
+                  float* count_err, int validate, void* buf, cudaStream_t st, const OutAdjust* adj) {
+    if (p.prec == 4) return launch_fft_t<float>(ctx, p, f, erode, out, cnt, count_err, validate, buf, st, adj);
+    return launch_fft_t<double>(ctx, p, f, erode, out, cnt, count_err, validate, buf, st, adj);
 }
 
 int launch_fft(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-               float* count_err, int validate, cudaStream_t st) {
+               float* count_err, int validate, cudaStream_t st, const OutAdjust* adj) {
     void* buf = nullptr;
     int rc = ctx_workspace(ctx, p.ws_bytes, &buf);
     if (rc) return rc;
     if (count_err) MORPH_CUDA_TRY(cudaMemsetAsync(count_err, 0, sizeof(float), st));
-    return launch_fft_in(ctx, p, f, erode, out, cnt, count_err, validate, buf, st);
+    return launch_fft_in(ctx, p, f, erode, out, cnt, count_err, validate, buf, st, adj);
 }
 
 }  // namespace morph

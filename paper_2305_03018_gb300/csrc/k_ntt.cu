@@ -263,6 +263,8 @@ struct NttArgs {
     uint32_t* buf;                  // [wave_tiles][Rf][Ny][Nx]
     int32_t* out;
     int32_t* out_cnt;
+    int out_add;                    // output adjustment of a composite's pass (OutAdjust)
+    const int32_t* out_sub;
     unsigned int* err;
     int kper;                       // grey frequencies per CTA of k_ntt_rows_fwd (multiple of its batch)
 };
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(512) k_ntt_range(const NttArgs a) {
         if (lane == 0) {
             const int dval = D < 0 ? 0 : D;
             const long long o = (static_cast<long long>(n) * a.h + i) * a.w + j;
-            a.out[o] = a.erode ? (a.L - 1 - dval) : dval;
+            a.out[o] = (a.erode ? (a.L - 1 - dval) : dval) + a.out_add - (a.out_sub ? a.out_sub[o] : 0);
             if (a.out_cnt) a.out_cnt[o] = D < 0 ? 0 : static_cast<int32_t>(cnt);
         }
     }
@@ -872,7 +874,7 @@ int build_ntt_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, Ntt
 }
 
 int launch_ntt_in(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-                  void* buf, cudaStream_t st) {
+                  void* buf, cudaStream_t st, const OutAdjust* adj) {
     NttArgs a;
     std::memset(&a, 0, sizeof(a));
     a.src = f->data;
@@ -907,6 +909,8 @@ int launch_ntt_in(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int er
     a.buf = static_cast<uint32_t*>(buf);
     a.out = out;
     a.out_cnt = cnt;
+    a.out_add = adj ? adj->add : 0;
+    a.out_sub = adj ? adj->sub : nullptr;
     a.err = ctx->d_err;
     const int Nx = p.ax.N, Ny = p.ay.N;
     const NttKernel rf = rows_fwd_for(p.kgroup), ri = rows_inv_for(p.kgroup);
@@ -942,11 +946,11 @@ int launch_ntt_in(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int er
 }
 
 int launch_ntt(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-               cudaStream_t st) {
+               cudaStream_t st, const OutAdjust* adj) {
     void* buf = nullptr;
     int rc = ctx_workspace(ctx, p.ws_bytes, &buf);
     if (rc) return rc;
-    return launch_ntt_in(ctx, p, f, erode, out, cnt, buf, st);
+    return launch_ntt_in(ctx, p, f, erode, out, cnt, buf, st, adj);
 }
 
 }  // namespace morph

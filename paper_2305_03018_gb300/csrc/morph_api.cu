@@ -1,6 +1,7 @@
 // C ABI of the library: context, argument validation (the S0 step: check
 // 0 <= b, 2 <= L, shapes), planning and dispatch to the kernels.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -264,35 +265,51 @@ static int get_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, in
 
 size_t planes_bytes(const morph_image* f) {
     const size_t w_pad = (static_cast<size_t>(f->w) + 62) & ~size_t(31);   // the direct plan's pitch
-    return static_cast<size_t>(f->n) * f->h * f->L * w_pad;
+    return (static_cast<size_t>(f->n) * f->h * f->L * w_pad + 255) & ~size_t(255);
 }
+
+size_t direct_ws_bytes(const morph_image* f) { return planes_bytes(f) + direct_band_bytes(f); }
 
 // Route for a request.  AUTO estimates each exact route's time on the host
 // (no device work) and takes the fastest among the FP8 direct route, the FP32
 // FFT route where its a-priori bound proves it exact, and the NTT route (exact
 // for any size it supports); the FP64 FFT route is the fallback where neither
 // transform route applies.  Each estimate is a fixed cost plus the route's
-// work at the rate fitted to GB300 runs over 35 shapes (images 64^2..4096^2,
-// L = 16 / 64 / 256, SEs 3^2..256^2; median error about 10 %):
-//   direct: 54 us + 1.07 x issued FLOP / 3e15 + 12.2 ns per tile pass
-//           (epilogue) + 0.76 ps per pixel level (encoder);
+// work at rates fitted to GB300 runs:
+//   direct: 70 us + 94.7 ns per MMA and 2.69 us per accumulation (epilogue)
+//           along the busiest SM (waves of units over the SMs) + 0.77 ps
+//           per pixel level (encoder), fitted over 180 shapes (images 64^2
+//           to 2048^2, L = 16 / 64 / 256, flat disks and full non-flat SEs
+//           3^2..63^2; 83 % within 1.5x).  The MMAs and accumulations depend
+//           on each unit's level band, which depends on the data; the
+//           estimate takes ceil((0.12 L + max b) / 16) chunks of 16 levels,
+//           the band of uniformly distributed pixel values;
 //   FFT32 : 70 us + FFT FLOP / 5.55e12;  FFT64: 92 us + FFT FLOP / 7.25e11;
-//   NTT   : 80 us + 1.48 x its own estimate (operations, bytes, CTAs).
-static double direct_time(const DirectPlan& dp, const morph_image* f) {
-    return 54e-6 + 1.07 * dp.issued_flop / 3.0e15 + 12.2e-9 * static_cast<double>(dp.tiles) * dp.T * dp.n_pass +
-           0.76e-12 * static_cast<double>(f->n) * f->h * f->w * f->L;
+//   NTT   : 80 us + 1.2 x its own estimate (operations, bytes, CTAs).
+static double direct_time(const DirectPlan& dp, const morph_image* f, int num_sms) {
+    if (dp.tiles <= 0) return 70e-6;
+    const int full = (dp.L + dp.Lc - 1) / dp.Lc;
+    const int est = static_cast<int>(std::ceil((0.12 * dp.L + dp.maxb) / dp.Lc));
+    const double nch = std::min(full, std::max(1, est));
+    const double waves = std::ceil(static_cast<double>(dp.tiles) / std::max(1, num_sms));
+    const double unit_mmas = dp.issued_flop / (2.0 * kDirectM * kDirectN * 32.0) / dp.tiles * nch / full;
+    return 70e-6 + 94.7e-9 * waves * unit_mmas + 2.69e-6 * waves * dp.n_pass * nch * dp.T +
+           0.77e-12 * static_cast<double>(f->n) * f->h * f->w * f->L;
 }
 
+// in_batch: the problem is one of a batch, whose FP8-route problems share one
+// encoder, band and tcgen05 launch, so the FP8 route's fixed cost is not this
+// problem's; the transform routes still launch their own kernels per problem.
 static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, int method,
-                        bool unproven, int* route) {
+                        bool unproven, int* route, bool in_batch = false) {
     if (method == MORPH_DIRECT_FP8) { *route = ROUTE_DIRECT; return MORPH_OK; }
     if (method == MORPH_FFT_F64) { *route = ROUTE_FFT64; return MORPH_OK; }
     if (method == MORPH_FFT_F32) { *route = ROUTE_FFT32; return MORPH_OK; }
     if (method == MORPH_NTT) { *route = ROUTE_NTT; return MORPH_OK; }
     if (method != MORPH_AUTO) return MORPH_E_INVAL;
-    const std::string key = "auto|" + plan_key(f, se, erode, 0);
+    const std::string key = (in_batch ? "autob|" : "auto|") + plan_key(f, se, erode, 0);
     if (ctx) {
-        auto tt = ctx->route_cache.find("tuned|" + key);          // a measured choice wins
+        auto tt = ctx->route_cache.find("tuned|auto|" + plan_key(f, se, erode, 0));   // a measured choice wins
         if (tt != ctx->route_cache.end()) { *route = tt->second; return MORPH_OK; }
         auto it = ctx->route_cache.find(key);
         if (it != ctx->route_cache.end()) { *route = it->second; return MORPH_OK; }
@@ -302,7 +319,7 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
     if (rc) return rc;
     *route = ROUTE_DIRECT;
     if (dp.taps > 0) {
-        double best = direct_time(dp, f);
+        double best = direct_time(dp, f, ctx ? ctx->num_sms : 152) - (in_batch ? 70e-6 : 0.0);
         FftPlan fp;
         const bool f32_ok = plan_fft_tiles(f, se, 4, false, &fp) == MORPH_OK;
         if (f32_ok) {
@@ -330,7 +347,7 @@ static int choose_route(morph_ctx* ctx, const morph_image* f, const morph_se* se
 }
 
 int prepare_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, const morph_opts* opts,
-                    std::shared_ptr<Plan>* plan) {
+                    std::shared_ptr<Plan>* plan, bool in_batch) {
     if (!ctx) return inval("null context");
     int rc = validate(f, b);
     if (rc) return rc;
@@ -339,13 +356,13 @@ int prepare_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int
     EffSE e;
     effective_se(b, erode, &e);
     int route = ROUTE_DIRECT;
-    rc = choose_route(ctx, f, &e.se, erode, method, unproven, &route);
+    rc = choose_route(ctx, f, &e.se, erode, method, unproven, &route, in_batch);
     if (rc) return rc;
     return get_plan(ctx, f, &e.se, erode, route, plan, route == ROUTE_FFT32 && unproven);
 }
 
 static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-                    const morph_opts* opts, cudaStream_t st);
+                    const morph_opts* opts, cudaStream_t st, const OutAdjust* adj = nullptr);
 
 // Autotuning (MORPH_F_AUTOTUNE with AUTO): time each exact route that the
 // models do not rule out -- FP8 direct, the FP32 FFT where its bound is
@@ -368,7 +385,7 @@ int tune_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int er
     if (rc) return rc;
     if (dp.taps == 0) return MORPH_OK;
     std::vector<std::pair<int, double>> cand;        // route, model estimate (s)
-    cand.push_back({ROUTE_DIRECT, direct_time(dp, f)});
+    cand.push_back({ROUTE_DIRECT, direct_time(dp, f, ctx ? ctx->num_sms : 152)});
     FftPlan fp;
     const bool f32_ok = plan_fft_tiles(f, &e.se, 4, false, &fp) == MORPH_OK;
     if (f32_ok) cand.push_back({ROUTE_FFT32, 70e-6 + fp.flop / 5.55e12});
@@ -419,7 +436,7 @@ int tune_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int er
 }
 
 int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
-            const morph_opts* opts, cudaStream_t st) {
+            const morph_opts* opts, cudaStream_t st, const OutAdjust* adj) {
     if (!out) return inval("null output");
     int rc = MORPH_OK;
     if (opts && (opts->flags & MORPH_F_AUTOTUNE) && opts->method == MORPH_AUTO) {
@@ -429,26 +446,27 @@ int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, 
     std::shared_ptr<Plan> plan;
     rc = prepare_problem(ctx, f, b, erode, opts, &plan);
     if (rc) return rc;
-    return run_plan(ctx, *plan, f, erode, out, cnt, opts, st);
+    return run_plan(ctx, *plan, f, erode, out, cnt, opts, st, adj);
 }
 
 // Steps 1-3 of one problem with a built plan.
 static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-                    const morph_opts* opts, cudaStream_t st) {
+                    const morph_opts* opts, cudaStream_t st, const OutAdjust* adj) {
     const Plan* plan = &pl;
     int rc = MORPH_OK;
     const long long npx = static_cast<long long>(f->n) * f->h * f->w;
-    if (plan->route == ROUTE_EMPTY) return launch_fill_empty(ctx, out, cnt, npx, erode ? f->L - 1 : 0, st);
-    if (plan->route == ROUTE_NTT) return launch_ntt(ctx, plan->ntt, f, erode, out, cnt, st);
+    if (plan->route == ROUTE_EMPTY) return launch_fill_empty(ctx, out, cnt, npx, erode ? f->L - 1 : 0, st, adj);
+    if (plan->route == ROUTE_NTT) return launch_ntt(ctx, plan->ntt, f, erode, out, cnt, st, adj);
     if (plan->route == ROUTE_FFT32 || plan->route == ROUTE_FFT64)
         return launch_fft(ctx, plan->fft, f, erode, out, cnt, opts ? opts->count_err : nullptr,
-                          (opts && (opts->flags & MORPH_F_VALIDATE)) ? 1 : 0, st);
+                          (opts && (opts->flags & MORPH_F_VALIDATE)) ? 1 : 0, st, adj);
 
     const DirectPlan& dp = plan->direct;
     void* ws = nullptr;
-    rc = ctx_workspace(ctx, planes_bytes(f), &ws);
+    rc = ctx_workspace(ctx, direct_ws_bytes(f), &ws);
     if (rc) return rc;
     uint8_t* planes = static_cast<uint8_t*>(ws);
+    DirectBand* band = reinterpret_cast<DirectBand*>(planes + planes_bytes(f));
 
     EncodeJob job;
     job.src = f->data;
@@ -472,10 +490,19 @@ static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int er
     std::memset(static_cast<void*>(&dl), 0, sizeof(dl));
     direct_fill_problem(dp, &dl.single, planes, out, cnt, 0, &rc);
     if (rc) return rc;
+    direct_fill_band(&dl.single, f, band);
+    if (adj) {
+        dl.single.out_add = adj->add;
+        dl.single.out_sub = adj->sub;
+    }
     dl.many = nullptr;
     dl.nprob = 1;
     dl.total_tiles = dp.tiles;
     dl.err = ctx->d_err;
+    dl.mma_count = ctx->d_mma;
+    dl.wait_ns = ctx->wait_ns;
+    rc = launch_band(ctx, dl, st);
+    if (rc) return rc;
     return launch_direct(ctx, dl, st);
 }
 
@@ -501,8 +528,12 @@ int morph_ctx_create(int device, morph_ctx** out) {
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_err, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMemset(c->d_err, 0, sizeof(unsigned int)) != cudaSuccess) {
+        cudaMemset(c->d_err, 0, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&c->d_mma, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->d_mma, 0, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
+        if (c->d_err) cudaFree(c->d_err);
+        if (c->d_mma) cudaFree(c->d_mma);
         delete c;
         return MORPH_E_NOMEM;
     }
@@ -528,6 +559,7 @@ int morph_ctx_destroy(morph_ctx* ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->ws2) cudaFree(ctx->ws2);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_mma) cudaFree(ctx->d_mma);
     delete ctx;
     return MORPH_OK;
 }
@@ -544,7 +576,7 @@ int morph_erode(morph_ctx* ctx, const morph_image* f, const morph_se* b, int32_t
 
 int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, int op, const morph_opts* opts,
                      morph_plan_info* out) {
-    if (!ctx || !out) return MORPH_E_INVAL;
+    if (!out) return MORPH_E_INVAL;
     int rc = validate(f, b);
     if (rc) return rc;
     const int method = opts ? opts->method : MORPH_AUTO;
@@ -577,10 +609,21 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
     }
     if (route == ROUTE_DIRECT) {
         std::shared_ptr<Plan> plan;
-        rc = get_plan(ctx, f, &e.se, erode, ROUTE_DIRECT, &plan);
-        if (rc) return rc;
-        const DirectPlan& d = plan->direct;
+        DirectPlan host_only;
+        const DirectPlan* dpp = &host_only;
+        if (ctx) {
+            rc = get_plan(ctx, f, &e.se, erode, ROUTE_DIRECT, &plan);
+            if (rc) return rc;
+            dpp = &plan->direct;
+        } else {
+            rc = plan_direct_host(f, &e.se, erode, &host_only);
+            if (rc) return rc;
+        }
+        const DirectPlan& d = *dpp;
         out->method = MORPH_DIRECT_FP8;
+        out->k_steps = d.ksteps;
+        out->level_chunks = (d.L + d.Lc - 1) / std::max(1, d.Lc);
+        out->ring_stages = direct_stages();
         out->groups = d.G;
         out->passes = d.n_pass;
         out->tile_w = d.J;
@@ -588,7 +631,7 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         out->unit_tiles = d.T;
         out->unit_blocks = d.nb;
         out->est_flop = d.issued_flop;
-        out->workspace_bytes = planes_bytes(f);
+        out->workspace_bytes = direct_ws_bytes(f);
     } else if (route == ROUTE_NTT) {
         NttPlan q;
         rc = plan_ntt_tiles(f, &e.se, &q);
@@ -657,7 +700,7 @@ int morph_workspace_size(morph_ctx* ctx, const morph_image* f, const morph_se* b
     rc = choose_route(ctx, f, &e.se, erode, method, unproven, &route);
     if (rc) return rc;
     if (route == ROUTE_DIRECT) {
-        *bytes = planes_bytes(f);
+        *bytes = direct_ws_bytes(f);
     } else if (route == ROUTE_NTT) {
         NttPlan q;
         rc = plan_ntt_tiles(f, &e.se, &q);
@@ -703,6 +746,22 @@ const char* morph_strerror(int s) {
 }
 
 uint64_t morph_launch_count(const morph_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int morph_ctx_set_wait_limit(morph_ctx* ctx, uint64_t ns) {
+    if (!ctx) return MORPH_E_INVAL;
+    ctx->wait_ns = static_cast<unsigned long long>(ns);
+    return MORPH_OK;
+}
+
+int morph_mma_count(morph_ctx* ctx, uint64_t* out) {
+    if (!ctx || !out) return MORPH_E_INVAL;
+    MORPH_CUDA_TRY(cudaSetDevice(ctx->device));
+    MORPH_CUDA_TRY(cudaDeviceSynchronize());
+    unsigned long long v = 0;
+    MORPH_CUDA_TRY(cudaMemcpy(&v, ctx->d_mma, sizeof(v), cudaMemcpyDeviceToHost));
+    *out = static_cast<uint64_t>(v);
+    return MORPH_OK;
+}
 
 int morph_profile_enable(morph_ctx* ctx, int on) {
     if (!ctx) return MORPH_E_INVAL;

@@ -31,6 +31,7 @@ struct morph_batch {
         int32_t* cnt;
         std::shared_ptr<Plan> plan;
         size_t planes_off = 0;
+        size_t band_off = 0;
     };
     std::vector<Item> items;
     std::vector<int> direct_order;       // items on the direct route, heaviest tiles first
@@ -104,7 +105,7 @@ int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts*
             int rc = tune_problem(ctx, &p[i].f, &p[i].se, p[i].op, opts, p[i].out, p[i].out_count, tune_stream);
             if (rc) return rc;
         }
-        int rc = prepare_problem(ctx, &p[i].f, &p[i].se, p[i].op, opts, &it.plan);
+        int rc = prepare_problem(ctx, &p[i].f, &p[i].se, p[i].op, opts, &it.plan, true);
         if (rc) return rc;
         if (it.plan->route == ROUTE_DIRECT) b->direct_order.push_back(i);
         else if (it.plan->route == ROUTE_EMPTY) b->empty_items.push_back(i);
@@ -124,6 +125,8 @@ int batch_setup(morph_ctx* ctx, const morph_problem* p, int n, const morph_opts*
     for (int i : b->direct_order) {
         b->items[i].planes_off = off;
         off = align_up(off + planes_bytes(&b->items[i].f), 256);
+        b->items[i].band_off = off;
+        off = align_up(off + direct_band_bytes(&b->items[i].f), 256);
     }
     size_t fft_need = 0;
     for (int i : b->fft_items) {
@@ -188,6 +191,7 @@ int batch_descriptors(morph_batch* b, uint8_t* ws) {
         int rc = MORPH_OK;
         direct_fill_problem(dp, &d, ws + it.planes_off, it.out, it.cnt, b->total_tiles, &rc);
         if (rc) return rc;
+        direct_fill_band(&d, &it.f, reinterpret_cast<DirectBand*>(ws + it.band_off));
         b->total_tiles += dp.tiles;
         b->probs.push_back(d);
     }
@@ -212,6 +216,8 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
         dl.nprob = static_cast<int>(b->probs.size());
         dl.total_tiles = b->total_tiles;
         dl.err = ctx->d_err;
+        dl.mma_count = ctx->d_mma;
+        dl.wait_ns = ctx->wait_ns;
         if (b->probs.size() == 1) {       // one problem: descriptor as a kernel parameter
             dl.single = b->probs[0];
             dl.many = nullptr;
@@ -219,6 +225,8 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
         int kind = b->probs.empty() ? 0 : direct_kind(b->probs[0]);
         for (const auto& d : b->probs)
             if (direct_kind(d) != kind) kind = 0;
+        rc = launch_band(ctx, dl, st);
+        if (rc) return rc;
         rc = launch_direct(ctx, dl, st, kind);
         if (rc) return rc;
     }

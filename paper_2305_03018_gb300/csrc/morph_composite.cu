@@ -5,38 +5,15 @@
 //   closing  (f . b) = (f (+) b) (-) b
 //   gradient         = (f (+) b) - (f (-) b)
 // The intermediate result is an int32 image; its values lie in
-// [-max b, L-1] (erosion) or [0, L-1+max b] (dilation), so it is shifted
-// into the tonal range [0, L + max b) before the second operation and the
-// shift is removed afterwards.  Every result is exact and unclamped.
+// [-max b, L-1] (erosion) or [0, L-1+max b] (dilation).  The opening's first
+// pass writes the erosion shifted by max b into the tonal range
+// [0, L + max b) of its second pass, whose epilogue removes the shift; the
+// gradient's second pass subtracts the stored erosion as it writes.  Every
+// result is exact and unclamped; where no tap is valid the second pass gives
+// the lowest (dilation) or highest (erosion) value of its input's range.
 #include "morph_internal.h"
 
 namespace morph {
-
-__global__ void k_add_const(const int32_t* __restrict__ in, int32_t* __restrict__ out, long long n, int add) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        out[k] = in[k] + add;
-}
-
-__global__ void k_sub(const int32_t* __restrict__ a, const int32_t* __restrict__ b, int32_t* __restrict__ out,
-                      long long n) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        out[k] = a[k] - b[k];
-}
-
-static unsigned blocks_for(morph_ctx* ctx, long long n) {
-    long long b = (n + 255) / 256;
-    if (b > ctx->num_sms * 8LL) b = ctx->num_sms * 8LL;
-    return static_cast<unsigned>(b < 1 ? 1 : b);
-}
-
-static int add_const(morph_ctx* ctx, const int32_t* in, int32_t* out, long long n, int add, cudaStream_t st) {
-    prof_begin(ctx, st, "k_add_const");
-    k_add_const<<<blocks_for(ctx, n), 256, 0, st>>>(in, out, n, add);
-    prof_end(ctx, st);
-    ctx->launches += 1;
-    MORPH_CUDA_TRY(cudaGetLastError());
-    return MORPH_OK;
-}
 
 static int ws2(morph_ctx* ctx, size_t bytes, int32_t** out) {
     void* p = nullptr;
@@ -62,7 +39,8 @@ static morph_image int_view(const morph_image* f, const int32_t* data, int L) {
     return g;
 }
 
-// op: 0 opening, 1 closing, 2 gradient
+// op: 0 opening, 1 closing, 2 gradient.  Two passes each; the tonal shift and
+// the gradient's difference are applied by the passes' own epilogues (OutAdjust).
 static int composite(morph_ctx* ctx, const morph_image* f, const morph_se* b, int op, int32_t* out,
                      const morph_opts* opts, cudaStream_t st) {
     if (!ctx || !f || !b || !out || !b->mask || !b->offset) return MORPH_E_INVAL;
@@ -72,17 +50,17 @@ static int composite(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
     if (n <= 0) return MORPH_E_INVAL;
     if (op != 2 && f->L + mb > 256) return MORPH_E_UNSUPPORTED;   // the second pass needs L + max b <= 256
     int32_t* t = nullptr;
-    int rc = ws2(ctx, sizeof(int32_t) * static_cast<size_t>(n) * 2, &t);
+    int rc = ws2(ctx, sizeof(int32_t) * static_cast<size_t>(n), &t);
     if (rc) return rc;
-    int32_t* t2 = t + n;
     if (op == 0) {
-        rc = run_one(ctx, f, b, 1, t, nullptr, opts, st);                 // E = f (-) b in [-mb, L-1]
-        if (!rc) rc = add_const(ctx, t, t2, n, mb, st);                   // E + mb in [0, L-1+mb]
+        OutAdjust up;
+        up.add = mb;
+        rc = run_one(ctx, f, b, 1, t, nullptr, opts, st, &up);           // E + mb, in [0, L-1+mb]
         if (rc) return rc;
-        const morph_image g = int_view(f, t2, f->L + mb);
-        rc = run_one(ctx, &g, b, 0, t, nullptr, opts, st);                // (E + mb) (+) b
-        if (!rc) rc = add_const(ctx, t, out, n, -mb, st);
-        return rc;
+        const morph_image g = int_view(f, t, f->L + mb);
+        OutAdjust down;
+        down.add = -mb;
+        return run_one(ctx, &g, b, 0, out, nullptr, opts, st, &down);     // ((E + mb) (+) b) - mb
     }
     if (op == 1) {
         rc = run_one(ctx, f, b, 0, t, nullptr, opts, st);                 // D = f (+) b in [0, L-1+mb]
@@ -90,15 +68,11 @@ static int composite(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         const morph_image g = int_view(f, t, f->L + mb);
         return run_one(ctx, &g, b, 1, out, nullptr, opts, st);            // D (-) b
     }
-    rc = run_one(ctx, f, b, 0, t, nullptr, opts, st);
-    if (!rc) rc = run_one(ctx, f, b, 1, t2, nullptr, opts, st);
+    rc = run_one(ctx, f, b, 1, t, nullptr, opts, st);                     // E
     if (rc) return rc;
-    prof_begin(ctx, st, "k_sub");
-    k_sub<<<blocks_for(ctx, n), 256, 0, st>>>(t, t2, out, n);
-    prof_end(ctx, st);
-    ctx->launches += 1;
-    MORPH_CUDA_TRY(cudaGetLastError());
-    return MORPH_OK;
+    OutAdjust diff;
+    diff.sub = t;
+    return run_one(ctx, f, b, 0, out, nullptr, opts, st, &diff);          // D - E
 }
 
 }  // namespace morph

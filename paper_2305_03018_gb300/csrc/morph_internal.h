@@ -45,20 +45,50 @@ struct EncodeJob {
     long long item_base;    // first work item of this job (batched launch)
 };
 
+// Output adjustment of one pass of a composite operator, applied by the route's
+// epilogue: the stored value is v + add - (sub ? sub[pixel] : 0), v the
+// dilation value (or the erosion's L - 1 - D).  The top counts are unchanged.
+struct OutAdjust {
+    int add = 0;
+    const int32_t* sub = nullptr;   // int32 [n][h][w], same layout as the output
+};
+
 // ------------------------------------------- FP8 tcgen05 direct route (Step 2)
 constexpr int kDirectMaxPasses = 32;
 constexpr long long kDirectSplitMinUnits = 2 * 152;   // split two-tile units only with two waves on 152 SMs
-constexpr int kDirectN = 256;        // MMA N: image rows x padded levels per tile
+constexpr int kDirectN = 256;        // MMA N: image rows x grey levels of one chunk
 constexpr int kDirectM = 128;        // MMA M: offset groups x output columns
+constexpr int kDirectLc = 16;        // grey levels per chunk of the N axis when L <= 16 (16 image rows)
+constexpr int kDirectLcBand = 8;     // ... when L > 16 and the unit's level band is computed (32 image rows)
+constexpr int kBandTapsMax = 264;    // taps of the per-unit lower bound on the top degree (16 x 16 cells + origin)
+
+// Per unit of a direct launch: hi = the largest level in the unit's input
+// window, lb = a lower bound on the smallest dilation value of the unit's
+// pixels (-1: none).  A product f(x - y) + b(y) that reaches a top degree has
+// level >= lb - b(y), so the pass of offset groups whose largest offset is
+// wmax contracts only the levels [max(0, lb - wmax), hi] (none when
+// lb - wmax > hi), in chunks of kDirectLc levels from the top: chunk c covers
+// hi - kDirectLc (c + 1) + 1 .. hi - kDirectLc c.
+struct DirectBand {
+    int hi;
+    int lb;
+};
 
 struct DirectProblemDev {
     CUtensorMap tmA;        // Toeplitz blocks: [blocks * 128 rows][128 B]
-    CUtensorMap tmB;        // planes: dims (w, L, h, n), box (128, Lpad, rows_n, 1)
+    CUtensorMap tmB;        // planes: dims (w, L, h, n), box (128, Lc, rows_n, 1)
     int32_t* out;           // [n][h][w]
     int32_t* out_cnt;       // nullable
-    const int* meta;        // pass_row_begin[n_pass+1], group_w[n_pass*8], rows[...]
+    int out_add;            // output adjustment (OutAdjust)
+    const int32_t* out_sub;
+    const int* meta;        // pass_row_begin[n_pass+1], group_w[n_pass*8], rows[...], band taps (3 ints each)
+    const DirectBand* band; // per unit; nullptr: every level, ceil(L / Lc) chunks
+    const void* src;        // the image (read by the band kernel)
+    int dtype;
+    long long row_stride, batch_stride;
+    int kh, maxb, band_tap_off, n_band_taps;
     int h, w, nimg, L;
-    int Lpad, rows_n, J, G;
+    int Lc, rows_n, J, G;
     int n_pass, nk, ksteps, kw;
     int oy, ox, e, erode;
     int shift;              // plane column of image column 0 (TMA x = image column + shift)
@@ -76,10 +106,13 @@ struct DirectLaunch {
     int nprob;
     long long total_tiles;
     unsigned int* err;
+    unsigned long long* mma_count;   // nullable: MMAs issued, added once per CTA
+    unsigned long long wait_ns;      // limit of each bounded wait; 0 = kWaitLimitNs
 };
 
 struct DirectPlan {
-    int L = 0, Lpad = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0, T = 1, split = 0, nb = 0;
+    int L = 0, Lc = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0, T = 1, split = 0, nb = 0;
+    int band_tap_off = 0, n_band_taps = 0;   // lower-bound taps (oy - r, ox - c, b) in meta
     int kh = 0, kw = 0, oy = 0, ox = 0, e = 0, erode = 0, shift = 0;
     int h = 0, w = 0, nimg = 0, w_pad = 0;
     int tiles_x = 0, tiles_y = 0;
@@ -91,7 +124,7 @@ struct DirectPlan {
     int* d_meta = nullptr;
     long long toeplitz_blocks = 0;
     CUtensorMap tmA;
-    double issued_flop = 0;           // dense MMA FLOP per launch
+    double issued_flop = 0;           // dense MMA FLOP per launch with every level (ceil(L / Lc) chunks)
     ~DirectPlan();
 };
 
@@ -190,6 +223,8 @@ struct morph_ctx {
     int device = 0;
     int num_sms = 0;
     unsigned int* d_err = nullptr;        // device error word
+    unsigned long long* d_mma = nullptr;  // MMAs issued by the direct route (measurement hook)
+    unsigned long long wait_ns = 0;       // limit of the kernels' bounded waits; 0 = the default
     void* ws = nullptr;                   // device workspace
     size_t ws_bytes = 0;
     void* ws2 = nullptr;                  // intermediate images of composite operators
@@ -212,7 +247,7 @@ namespace morph {
 // context: each group of kernels is set up once per device.  kernels_ready
 // tells whether `group` is set up on `device`; mark_kernels_ready records it
 // after the setup succeeded (a race only repeats the idempotent setup).
-enum KernelGroup { kGroupDirect = 0, kGroupFft32, kGroupFft64, kGroupFftPlane, kGroupNtt, kGroupCount };
+enum KernelGroup { kGroupDirect = 0, kGroupFft32, kGroupFft64, kGroupFftPlane, kGroupNtt, kGroupBand, kGroupCount };
 bool kernels_ready(int device, KernelGroup group);
 void mark_kernels_ready(int device, KernelGroup group);
 
@@ -233,7 +268,7 @@ int encode_tmap(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base, co
 int launch_encode(morph_ctx* ctx, const EncodeJob* jobs, int njobs, long long total_items,
                   EncodeJob* d_jobs, cudaStream_t st);
 int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int erode, DirectPlan* p);
-int plan_direct_host(const morph_image* f, const morph_se* se, int erode, DirectPlan* p);
+int plan_direct_host(const morph_image* f, const morph_se* se, int erode, DirectPlan* p, int dev_bound = -1);
 // uniform_T: tiles per unit shared by every problem of a batched launch (1 or 2), 0 if mixed
 // unit kind: 1 = one tile, 2 = two tiles in one K block, 3 = two split tiles; 0 = per problem
 int direct_kind(const DirectProblemDev& d);
@@ -242,30 +277,39 @@ int direct_smem_bytes(int stages);
 int direct_stages();
 void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,
                          int32_t* out_cnt, long long tile_base, int* status);
-int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st);
+// the image and the per-unit band buffer of a problem (band may be nullptr: every level)
+void direct_fill_band(DirectProblemDev* d, const morph_image* f, DirectBand* band);
+// bytes of the per-unit band buffer for an image of this shape (any plan)
+size_t direct_band_bytes(const morph_image* f);
+// per-unit grey-level bands of every problem of a direct launch (before launch_direct, same stream)
+int launch_band(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st);
+int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st,
+                      const OutAdjust* adj = nullptr);
 // validation, erosion reflection, route choice and (cached) plan of one problem
 int prepare_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, const morph_opts* opts,
-                    std::shared_ptr<Plan>* plan);
+                    std::shared_ptr<Plan>* plan, bool in_batch = false);
 size_t planes_bytes(const morph_image* f);
+// workspace of one direct-route call: the planes, then the per-unit band buffer
+size_t direct_ws_bytes(const morph_image* f);
 // time the exact routes of one AUTO problem on its own buffers and cache the fastest (MORPH_F_AUTOTUNE)
 int tune_problem(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, const morph_opts* opts,
                  int32_t* out, int32_t* cnt, cudaStream_t st);
 // one dilation (erode = 0) or erosion (erode = 1), the body of morph_dilate / morph_erode
 int run_one(morph_ctx* ctx, const morph_image* f, const morph_se* b, int erode, int32_t* out, int32_t* cnt,
-            const morph_opts* opts, cudaStream_t st);
+            const morph_opts* opts, cudaStream_t st, const OutAdjust* adj = nullptr);
 int plan_fft_tiles(const morph_image* f, const morph_se* se, int prec, bool unproven, FftPlan* p);
 int build_fft_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, int prec, bool unproven, FftPlan* p);
 int launch_fft(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-               float* count_err, int validate, cudaStream_t st);
+               float* count_err, int validate, cudaStream_t st, const OutAdjust* adj = nullptr);
 int launch_fft_in(morph_ctx* ctx, const FftPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-                  float* count_err, int validate, void* buf, cudaStream_t st);
+                  float* count_err, int validate, void* buf, cudaStream_t st, const OutAdjust* adj = nullptr);
 int plan_ntt_tiles(const morph_image* f, const morph_se* se, NttPlan* p);
 double ntt_time_estimate(const NttPlan& p);
 int build_ntt_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, NttPlan* p);
 int launch_ntt(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-               cudaStream_t st);
+               cudaStream_t st, const OutAdjust* adj = nullptr);
 int launch_ntt_in(morph_ctx* ctx, const NttPlan& p, const morph_image* f, int erode, int32_t* out, int32_t* cnt,
-                  void* buf, cudaStream_t st);
+                  void* buf, cudaStream_t st, const OutAdjust* adj = nullptr);
 // device workspace of morph_dilate_backward / morph_erode_backward (shares + partial sums)
 size_t backward_workspace_bytes(const morph_image* f, const morph_se* b);
 double fft_error_bound(const FftAxis& ax, const FftAxis& ay, const FftAxis& ar, double sqrtP, int taps, double u);

@@ -144,9 +144,8 @@ int check_args(const morph_image* f, const morph_se* b, int op, const int32_t* o
 int plan_inline(const morph_image* f, const std::vector<uint8_t>& mask, const std::vector<int>& off, int kh, int kw,
                 int oy, int ox, int erode, DirectPlan* p, InlineSE* ise) {
     p->L = f->L;
-    p->Lpad = 16;
-    while (p->Lpad < f->L) p->Lpad <<= 1;
-    p->rows_n = kDirectN / p->Lpad;
+    p->Lc = kDirectLc;                  // every level, in chunks of Lc (no band buffer)
+    p->rows_n = kDirectN / kDirectLc;
     p->kh = kh;
     p->kw = kw;
     p->oy = oy;

@@ -1,9 +1,10 @@
 // Inline-PTX helpers for sm_103a: mbarriers, TMA bulk-tensor copies and the
 // tcgen05 (5th-generation tensor core) instructions with TMEM accumulators.
 //
-// Every wait is bounded: a spin that exceeds kWaitLimitNs records
-// MORPH_DEVERR_TIMEOUT in the caller's error word and returns false, so no
-// kernel of this library can hang the GPU on a barrier.
+// Every wait is bounded: a spin that exceeds its limit (kWaitLimitNs unless
+// the launch sets a shorter one) records MORPH_DEVERR_TIMEOUT in the caller's
+// error word and returns false, so no kernel of this library can hang the GPU
+// on a barrier.
 #pragma once
 #include <cstdint>
 #include <cuda.h>
@@ -14,7 +15,7 @@
 
 namespace morph {
 
-constexpr unsigned long long kWaitLimitNs = 4000000000ull;   // 4 s per wait
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;   // 4 s per wait (default)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -55,17 +56,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait on the phase with the given parity.  Returns false (and
-// raises the CTA abort flag and the device error word) after kWaitLimitNs, or
-// as soon as another role of the CTA has aborted.
+// raises the CTA abort flag and the device error word) after limit_ns, or as
+// soon as another role of the CTA has aborted.  Limits under a millisecond
+// (a failure-handling test's) are checked on every spin.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          unsigned int* err) {
+                                          unsigned int* err, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
+    const uint32_t every = limit_ns < 1000000ull ? 0u : 63u;
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0u) {
+        if ((it & every) == 0u) {
             if (*abort_flag) return false;
-            if (globaltimer() - t0 > kWaitLimitNs) {
+            if (globaltimer() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicOr(err, MORPH_DEVERR_TIMEOUT);
                 return false;
@@ -172,6 +175,15 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float (&v)[16
         : "r"(taddr) : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr) : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Shared-memory matrix descriptor, K-major, 128-byte swizzle: rows of 128 B,

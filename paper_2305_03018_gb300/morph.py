@@ -61,7 +61,8 @@ class morph_plan_info(ctypes.Structure):
                 ("fft_nx", ctypes.c_int), ("fft_ny", ctypes.c_int), ("groups", ctypes.c_int),
                 ("passes", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
                 ("est_flop", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
-                ("unit_tiles", ctypes.c_int), ("unit_blocks", ctypes.c_int)]
+                ("unit_tiles", ctypes.c_int), ("unit_blocks", ctypes.c_int),
+                ("k_steps", ctypes.c_int), ("level_chunks", ctypes.c_int), ("ring_stages", ctypes.c_int)]
 
 
 class morph_problem(ctypes.Structure):
@@ -111,6 +112,8 @@ _SIGS = {
     "morph_stream_check": (ctypes.c_int, [_P, _P]),
     "morph_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "morph_launch_count": (ctypes.c_uint64, [_P]),
+    "morph_mma_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "morph_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "morph_run_noalloc": (ctypes.c_int, [ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), ctypes.c_int, _P, _P,
                                          _P, _P]),
     "morph_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -270,6 +273,16 @@ def morph_strerror(status: int) -> str:
 
 def morph_launch_count(ctx) -> int:
     return int(load_library().morph_launch_count(ctx))
+
+
+def morph_ctx_set_wait_limit(ctx, ns: int) -> int:
+    return load_library().morph_ctx_set_wait_limit(ctx, int(ns))
+
+
+def morph_mma_count(ctx) -> int:
+    v = ctypes.c_uint64(0)
+    check(load_library().morph_mma_count(ctx, ctypes.byref(v)), "morph_mma_count")
+    return int(v.value)
 
 
 def morph_run_noalloc(image, se, op, out_ptr, cnt_ptr, status_ptr, stream) -> int:
@@ -524,6 +537,14 @@ class Context:
 
     def launches(self) -> int:
         return morph_launch_count(self.handle)
+
+    def set_wait_limit(self, ns: int):
+        """Limit of the kernels' bounded waits (0 = the default 4 s); a failure-handling hook."""
+        check(morph_ctx_set_wait_limit(self.handle, ns), "morph_ctx_set_wait_limit")
+
+    def mma_count(self) -> int:
+        """tcgen05 MMAs the FP8 direct route issued through this context (synchronises)."""
+        return morph_mma_count(self.handle)
 
     def profile(self, on: bool):
         check(morph_profile_enable(self.handle, on), "morph_profile_enable")

@@ -1,10 +1,11 @@
 """GPU composite operators (opening, closing, Beucher gradient) against the
-oracle compositions, bit-exact."""
+oracle's composites (the definitions applied twice on the raw integers),
+bit-exact."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2305_03018_gb300 import workloads as wl
-from tests.test_oracle_composite import closing, gradient, opening
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,10 +28,10 @@ def test_composites_bit_exact(case, method):
     f = g.integers(0, L, size=(N, H, W)).astype(np.uint8)
     se = wl.se_random(g, kh, kw, p_in, mo, origin=origin)
     ft = torch.from_numpy(f).cuda()
-    for which, ref in (("open", opening), ("close", closing), ("gradient", gradient)):
+    for which, ref in (("open", oracle.opening), ("close", oracle.closing), ("gradient", oracle.gradient)):
         got = ctx.composite(which, ft, L, se, method=method)
         ctx.check()
-        exp = ref(f.astype(np.int32), L, se)
+        exp = ref(f, L, se.mask, se.offset, se.origin)
         assert np.array_equal(got.cpu().numpy(), exp), which
 
 

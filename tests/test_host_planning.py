@@ -30,12 +30,18 @@ def _ws(im, se, op, method="auto"):
     return M.morph_workspace_size(None, im, sv.c, op, M.make_opts(method))
 
 
+def _band_bytes(n, h, w):
+    # one (level, chunks) int pair per unit of 16 image rows by at least 16 columns, 256-byte rounded
+    return -(-n * -(-h // 16) * -(-w // 16) * 8 // 256) * 256
+
+
 def test_direct_and_backward_sizes_follow_their_layouts(bwd_chunks):
     g = wl.rng(61)
     se = wl.se_random(g, 9, 7, 0.6, 5)
     im = _img(2, 200, 300, 64)
-    # indicator planes: n h L round32(w + 31) bytes (room for the column shift that aligns K windows)
-    assert _ws(im, se, 0, "direct_fp8") == _ws(im, se, 1, "direct_fp8") == 2 * 200 * 64 * 352
+    # indicator planes: n h L round32(w + 31) bytes (room for the column shift that aligns K windows),
+    # then the per-unit grey-level bands
+    assert _ws(im, se, 0, "direct_fp8") == _ws(im, se, 1, "direct_fp8") == 2 * 200 * 64 * 352 + _band_bytes(2, 200, 300)
     # backward: a float share per pixel (256-byte rounded) + a partial sum per (tap, chunk)
     ntaps = int(np.count_nonzero(se.mask))
     exp = -(-2 * 200 * 300 * 4 // 256) * 256 + ntaps * bwd_chunks(2, 200, 300, ntaps) * 4
@@ -92,7 +98,7 @@ def test_huge_offsets_plan_only_the_fp8_route():
     o = np.array([[0, 65535, 7], [3, 0, 40000], [1, 2, 3]], np.int32)
     se = wl.SE(m, o, (1, 1), "huge")
     im = _img(1, 64, 64, 256)
-    assert _ws(im, se, 0, "auto") == _ws(im, se, 0, "direct_fp8") == 64 * 256 * 96   # planes: h L round32(w + 31)
+    assert _ws(im, se, 0, "auto") == _ws(im, se, 0, "direct_fp8") == 64 * 256 * 96 + _band_bytes(1, 64, 64)
     for method in ("ntt", "fft_f64"):
         with pytest.raises(M.MorphError) as ei:
             _ws(im, se, 0, method)

@@ -8,7 +8,8 @@ its invariants for every window width the planner can produce:
   block staged with that B block or the one before; every (tile, K step) pair
   is issued exactly once, and the row stages ceil((J + 32 ksteps) / 128)
   blocks;
-* the stage ring (4 slots, one "landed" and one "consumed" barrier each):
+* the stage ring (STAGES slots, the library's own ring depth, one "landed" and
+  one "consumed" barrier each):
   with split units a stage is released after the next stage's MMAs.  A
   random-interleaving model of the producer, the MMA issuer and the
   asynchronous releases never deadlocks and never lets the producer refill
@@ -19,7 +20,30 @@ import random
 
 import pytest
 
-STAGES = 4
+def _ring_stages():
+    """The direct kernel's ring depth as the library reports it (host-only plan query)."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_2305_03018_gb300 import morph as M
+    from paper_2305_03018_gb300 import workloads as wl
+    buf = ctypes.create_string_buffer(16)
+    im = M.morph_image()
+    im.data = ctypes.addressof(buf)
+    im.dtype = M.MORPH_U8
+    im.n, im.h, im.w, im.row_stride, im.batch_stride, im.L = 1, 64, 64, 64, 64 * 64, 16
+    sv = M.se_view(wl.se_flat_square(3))
+    return M.morph_plan_query(None, im, sv.c, 0, M.make_opts("direct_fp8")).ring_stages
+
+
+_STAGES = []
+
+
+def _stages():
+    if not _STAGES:
+        _STAGES.append(_ring_stages())
+    return _STAGES[0]
 
 
 def split_schedule(J, ksteps):
@@ -55,6 +79,7 @@ def test_split_schedule_covers_each_k_step_once(J):
 
 def _ring_model(units, seed):
     """units: (blocks per SE row, split) per row, in launch order."""
+    STAGES = _stages()
     rnd = random.Random(seed)
     program = [(r, kc) for r, (nb, _) in enumerate(units) for kc in range(nb)]
     slot = [None] * STAGES
@@ -115,3 +140,182 @@ def test_stage_ring_never_deadlocks_or_overwrites():
         units = [rnd.choice(kinds) for _ in range(rnd.randint(1, 10))]
         for seed in range(4):
             _ring_model(units, 97 * trial + seed)
+
+
+def _plan(kw, nlev, h=2048, w=2048):
+    """The library's own host-side plan (no GPU) of a one-row SE of width kw
+    with nlev offset levels, on an h x w image with L = 64."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_2305_03018_gb300 import morph as M
+    from paper_2305_03018_gb300 import workloads as wl
+    buf = ctypes.create_string_buffer(16)
+    im = M.morph_image()
+    im.data = ctypes.addressof(buf)
+    im.dtype = M.MORPH_U8
+    im.n, im.h, im.w = 1, h, w
+    im.row_stride, im.batch_stride, im.L = w, h * w, 64
+    m = np.ones((1, kw), np.uint8)
+    off = (np.arange(kw) % nlev).astype(np.int32)[None]
+    sv = M.se_view(wl.SE(m, off, (0, kw // 2)))
+    return M.morph_plan_query(None, im, sv.c, 0, M.make_opts("direct_fp8"))
+
+
+@pytest.mark.parametrize("nlev", [1, 2, 3, 5, 8])
+def test_model_matches_the_library_plan(nlev):
+    # the schedule above is checked against the (J, K steps, staged blocks, unit kind) that the
+    # library itself plans, so the model cannot drift from the kernel's planner unnoticed
+    kinds = []
+    for kw in list(range(1, 70, 3)) + [100, 130, 200, 257, 400, 512]:
+        info = _plan(kw, nlev)
+        J, ks, nb, T = info.tile_w, info.k_steps, info.unit_blocks, info.unit_tiles
+        # L = 64: units of 32 image rows x 8-level chunks, 8 of them when a band holds every level
+        assert info.groups * J == 128 and info.tile_h == 32 and info.level_chunks == 8
+        assert ks == (J + kw - 1 + 31) // 32
+        nk = (J + kw - 1 + 127) // 128
+        split = T == 2 and J + kw - 1 > 128
+        if split:
+            got_nb, sched = split_schedule(J, ks)
+            assert got_nb == nb < 2 * nk and J >= 32
+            assert {(tt, k) for _, tt, k, _, _ in sched} == {(tt, k) for tt in range(2) for k in range(ks)}
+        elif T == 2:
+            assert 2 * J + kw - 1 <= 128 and J + 32 * ks <= 128 and nb == nk == 1
+        else:
+            assert nb == nk
+        kinds.append((nb, split))
+    for seed in range(6):
+        _ring_model(kinds, seed)
+
+
+# ------------------------------------------------------------------ abort path
+def _abort_model(n_units, blocks_per_unit, seed, inject_p, always_drain=True):
+    """The three roles of k_direct_fp8 (one tile per unit, accumulator slots used
+    alternately) with one injected wait timeout at a random blocked wait.  Waits
+    fail once the CTA's abort flag is up.  Copies land in any order; MMA batches
+    complete in issue order, each then arriving on its barrier.  Returns the
+    copies and MMA batches still in flight when all roles reach the final barrier
+    (after which TMEM is freed and the CTA exits), or raises on a deadlock."""
+    STAGES = _stages()
+    rnd = random.Random(seed)
+    st = {"abort": False, "injected": False}
+    landed = set()            # copy ids that have landed
+    inflight_copies = set()
+    mma_q = []                # in-flight MMA batches: ("empty", slot) / ("tfull", slot) / ("drain",)
+    released = [0] * STAGES   # empty-barrier phases completed per stage slot
+    tfull = [0, 0]            # accumulator-full arrivals per TMEM slot
+    tempty = [0, 0]           # accumulator-free arrivals per TMEM slot (epilogue)
+    drained = [False]
+    program = [(u, kc) for u in range(n_units) for kc in range(blocks_per_unit)]
+
+    def wait(cond):
+        while not cond():
+            if st["abort"]:
+                return False
+            if not st["injected"] and rnd.random() < inject_p:
+                st["injected"] = st["abort"] = True      # this wait reached its limit
+                return False
+            yield None
+        return True
+
+    def producer():
+        it, ok = 0, True
+        for _ in program:
+            s = it % STAGES
+            ok = yield from wait(lambda: released[s] >= it // STAGES)
+            if not ok:
+                break
+            inflight_copies.add(it)
+            it += 1
+        if always_drain or not ok:
+            for k in range(max(0, it - STAGES), it):
+                while k in inflight_copies:
+                    yield None
+
+    def mma():
+        it, use, nxt, ok = 0, [0, 0], 0, True
+        for u in range(n_units):
+            s0, nxt = nxt, nxt ^ 1
+            ok = yield from wait(lambda: tempty[s0] >= use[s0])
+            if not ok:
+                break
+            for kc in range(blocks_per_unit):
+                k = it
+                ok = yield from wait(lambda: k in landed)
+                if not ok:
+                    break
+                mma_q.append(("empty", k % STAGES))
+                it += 1
+            if not ok:
+                break
+            mma_q.append(("tfull", s0))
+            use[s0] += 1
+        if always_drain or not ok:
+            mma_q.append(("drain",))
+            while not drained[0]:
+                yield None
+
+    def epilogue():
+        use, nxt = [0, 0], 0
+        for u in range(n_units):
+            s0, nxt = nxt, nxt ^ 1
+            ok = yield from wait(lambda: tfull[s0] > use[s0])
+            if not ok:
+                break
+            tempty[s0] += 1
+            use[s0] += 1
+
+    roles = [producer(), mma(), epilogue()]
+    done = [False] * 3
+    steps = 0
+    while not all(done):
+        steps += 1
+        assert steps < 200000, "deadlock"
+        c = rnd.random()
+        if c < 0.25 and inflight_copies:
+            k = rnd.choice(sorted(inflight_copies))       # a copy lands
+            inflight_copies.discard(k)
+            landed.add(k)
+        elif c < 0.45 and mma_q:
+            ev = mma_q.pop(0)                             # the oldest MMA batch completes
+            if ev[0] == "empty":
+                released[ev[1]] += 1
+            elif ev[0] == "tfull":
+                tfull[ev[1]] += 1
+            else:
+                drained[0] = True
+        else:
+            r = rnd.randrange(3)
+            if not done[r]:
+                try:
+                    next(roles[r])
+                except StopIteration:
+                    done[r] = True
+    return len(inflight_copies), len(mma_q)
+
+
+def test_abort_drains_every_copy_and_mma_before_exit():
+    # a timeout at any wait of any role: when all roles meet at the final barrier, no TMA copy
+    # can still land in shared memory and no MMA can still write TMEM
+    hits = 0
+    for trial in range(600):
+        n_units = 1 + trial % 5
+        blocks = 1 + (trial // 5) % 4
+        copies, mmas = _abort_model(n_units, blocks, trial, inject_p=0.02)
+        assert copies == 0 and mmas == 0, (trial, copies, mmas)
+        hits += 1
+    assert hits == 600
+
+
+def test_abort_model_catches_a_drain_taken_only_by_the_role_that_failed():
+    # planted mistake, on the CPU: drain only when this role's own wait failed.  When the
+    # epilogue gives up after the MMA issuer has run to its end, MMAs are still in flight at
+    # the final barrier, which the model must see
+    found = False
+    for trial in range(3000):
+        copies, mmas = _abort_model(2 + trial % 3, 1 + trial % 2, trial, inject_p=0.05, always_drain=False)
+        if copies or mmas:
+            found = True
+            break
+    assert found
