@@ -81,6 +81,19 @@ typedef struct {
     const int32_t *offset;   /* host, kh*kw, >= 0 where mask != 0 */
 } morph_se;
 
+/* A structuring element whose offsets live in device memory -- a learnable
+ * layer's parameter -- so that no call has to copy them to the host (which
+ * would wait for the device).  The mask and the bound are host values; the
+ * plan depends on them only.  Offsets outside [0, max_offset] at taps are a
+ * data error reported by morph_stream_check (MORPH_E_RANGE). */
+typedef struct {
+    int kh, kw;              /* box size, 1..512 each */
+    int oy, ox;              /* box entry of the spatial origin */
+    const uint8_t *mask;     /* host, kh*kw, row-major */
+    const int32_t *offset;   /* DEVICE, kh*kw int32, in [0, max_offset] where mask != 0 */
+    int max_offset;          /* host bound on the offsets, 0..255 */
+} morph_se_dev;
+
 /* ------------------------------------------------------------ options */
 enum morph_method {
     MORPH_AUTO = 0,          /* planner picks the fastest exact back-end */
@@ -176,6 +189,18 @@ int morph_dilate(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_
 int morph_erode(morph_ctx *ctx, const morph_image *f, const morph_se *b, int32_t *out,
                 int32_t *out_count, const morph_opts *opts, morph_stream_t stream);
 
+/* Dilation (Eq. 6new / Eq. 6) and erosion (Eq. Erosion) by an SE with
+ * device-resident offsets, on the FP8 tensor-core route; arguments and results
+ * as morph_dilate / morph_erode.  Every offset level 0..max_offset is planned
+ * for, so a tight bound costs less.  The plan (cached per mask, bound and
+ * shape) is built on the first call; later calls only read the offsets on the
+ * device (each call writes the SE's Toeplitz blocks into the context's
+ * workspace), so the call neither synchronizes nor copies to the host. */
+int morph_dilate_dev_se(morph_ctx *ctx, const morph_image *f, const morph_se_dev *b, int32_t *out,
+                        int32_t *out_count, morph_stream_t stream);
+int morph_erode_dev_se(morph_ctx *ctx, const morph_image *f, const morph_se_dev *b, int32_t *out,
+                       int32_t *out_count, morph_stream_t stream);
+
 /* 3-D volumes (the method is stated for N-D images, Sec. 2.1 and Sec. 3). */
 typedef struct {
     const void *data;        /* device pointer to voxel (0,0,0) of volume 0 */
@@ -246,6 +271,16 @@ int morph_dilate_backward(morph_ctx *ctx, const morph_image *f, const morph_se *
 int morph_erode_backward(morph_ctx *ctx, const morph_image *f, const morph_se *b,
                          const int32_t *E, const int32_t *cE, const float *grad_out,
                          float *grad_in, float *grad_se, morph_stream_t stream);
+
+/* The two backward passes for an SE with device-resident offsets (the outputs
+ * of morph_dilate_dev_se / morph_erode_dev_se); arguments otherwise as
+ * morph_dilate_backward / morph_erode_backward.  No host copy, no sync. */
+int morph_dilate_backward_dev_se(morph_ctx *ctx, const morph_image *f, const morph_se_dev *b,
+                                 const int32_t *D, const int32_t *cD, const float *grad_out,
+                                 float *grad_in, float *grad_se, morph_stream_t stream);
+int morph_erode_backward_dev_se(morph_ctx *ctx, const morph_image *f, const morph_se_dev *b,
+                                const int32_t *E, const int32_t *cE, const float *grad_out,
+                                float *grad_in, float *grad_se, morph_stream_t stream);
 
 /* One problem of a heterogeneous batch. */
 typedef struct {

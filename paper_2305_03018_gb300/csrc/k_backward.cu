@@ -36,6 +36,18 @@ struct BwdRow {
     int dy, t0, t1;       // SE row offset and its taps [t0, t1) in the tap list
 };
 
+// A device-resident SE's tap list for one call: the cached list (offsets 0)
+// with each tap's offset read from the caller's device array, clamped into
+// [0, bound] (an offset outside it is reported by the forward call).
+__global__ void k_bwd_taps_dev(const BwdTap* __restrict__ src, int ntaps, const int32_t* __restrict__ off, int bound,
+                               BwdTap* __restrict__ dst) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntaps; t += gridDim.x * blockDim.x) {
+        BwdTap tp = src[t];
+        tp.b = min(max(off[tp.box], 0), bound);
+        dst[t] = tp;
+    }
+}
+
 struct BwdImage {
     const void* f;
     int dtype, n, h, w;
@@ -351,20 +363,25 @@ size_t morph::backward_workspace_bytes(const morph_image* f, const morph_se* b) 
     return share_bytes(f) + static_cast<size_t>(ntaps) * static_cast<size_t>(L.nchunks) * sizeof(float);
 }
 
+// dev_off != nullptr: the SE's offsets are in device memory (b->offset is not
+// read) and lie in [0, dev_bound]; the cached tap list then depends on the mask
+// only and each call writes its offsets into a workspace copy.
 static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b, const int32_t* D,
                          const int32_t* cD, const float* grad_out, float* grad_in, float* grad_se,
-                         morph_stream_t stream, int sgn) {
+                         morph_stream_t stream, int sgn, const int32_t* dev_off = nullptr, int dev_bound = 0) {
     if (!ctx || !f || !b || !f->data || !D || !cD || !grad_out) return MORPH_E_INVAL;
     if (f->dtype < MORPH_U8 || f->dtype > MORPH_I32 || f->n < 1 || f->h < 1 || f->w < 1) return MORPH_E_INVAL;
     if (f->row_stride < f->w || f->batch_stride < static_cast<int64_t>(f->h - 1) * f->row_stride + f->w)
         return MORPH_E_INVAL;
-    if (b->kh < 1 || b->kw < 1 || b->kh > 512 || b->kw > 512 || !b->mask || !b->offset) return MORPH_E_INVAL;
+    if (b->kh < 1 || b->kw < 1 || b->kh > 512 || b->kw > 512 || !b->mask || (!b->offset && !dev_off))
+        return MORPH_E_INVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // tap list, cached per SE
-    std::string key = "bwd|";
+    // tap list, cached per SE (per mask for device-resident offsets)
+    std::string key = dev_off ? "bwddev|" : "bwd|";
     key.append(reinterpret_cast<const char*>(&b->kh), 4 * sizeof(int));
     key.append(reinterpret_cast<const char*>(b->mask), static_cast<size_t>(b->kh) * b->kw);
-    key.append(reinterpret_cast<const char*>(b->offset), static_cast<size_t>(b->kh) * b->kw * sizeof(int32_t));
+    if (!dev_off)
+        key.append(reinterpret_cast<const char*>(b->offset), static_cast<size_t>(b->kh) * b->kw * sizeof(int32_t));
     std::shared_ptr<BwdPlan> plan;
     auto it = ctx->aux_plans.find(key);
     if (it != ctx->aux_plans.end()) {
@@ -375,8 +392,8 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
             for (int c = 0; c < b->kw; ++c) {
                 const int t = r * b->kw + c;
                 if (!b->mask[t]) continue;
-                if (b->offset[t] < 0) return MORPH_E_INVAL;
-                taps.push_back(BwdTap{r - b->oy, c - b->ox, b->offset[t], t});
+                if (!dev_off && b->offset[t] < 0) return MORPH_E_INVAL;
+                taps.push_back(BwdTap{r - b->oy, c - b->ox, dev_off ? 0 : b->offset[t], t});
             }
         if (taps.size() > 65535) return MORPH_E_UNSUPPORTED;   // one grid row of partial sums per tap
         plan = std::make_shared<BwdPlan>();
@@ -408,10 +425,22 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
     // workspace: q (one float per pixel), then the partial sums
     const size_t q_bytes = share_bytes(f);
     const size_t part_bytes = grad_se ? static_cast<size_t>(plan->ntaps) * nchunks * sizeof(float) : 0;
+    const size_t taps_bytes = dev_off ? (static_cast<size_t>(plan->ntaps) * sizeof(BwdTap) + 255) & ~size_t(255) : 0;
     void* ws = nullptr;
-    int rc = ctx_workspace(ctx, q_bytes + part_bytes, &ws);
+    int rc = ctx_workspace(ctx, q_bytes + part_bytes + taps_bytes, &ws);
     if (rc) return rc;
     float* q = static_cast<float*>(ws);
+    const BwdTap* taps_dev = plan->d_taps;
+    if (dev_off && plan->ntaps > 0) {
+        BwdTap* dst = reinterpret_cast<BwdTap*>(static_cast<unsigned char*>(ws) + q_bytes + part_bytes);
+        const unsigned nb = static_cast<unsigned>(std::min(64, (plan->ntaps + 255) / 256));
+        prof_begin(ctx, st, "k_bwd_taps_dev");
+        k_bwd_taps_dev<<<nb, 256, 0, st>>>(plan->d_taps, plan->ntaps, dev_off, dev_bound, dst);
+        prof_end(ctx, st);
+        ctx->launches += 1;
+        MORPH_CUDA_TRY(cudaGetLastError());
+        taps_dev = dst;
+    }
     if (plan->ntaps > 0) {
         const unsigned blocks = static_cast<unsigned>(std::min<long long>((total + 255) / 256, ctx->num_sms * 16LL));
         prof_begin(ctx, st, "k_bwd_share");
@@ -426,7 +455,7 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
         const size_t smem = sizeof(float) * (kSeThreads / 32) * plan->ntaps;
         prof_begin(ctx, st, "k_bwd_fused");
         const BwdFusedKernel kf = sgn > 0 ? fused_kernel<1>(f->dtype, lay.M) : fused_kernel<-1>(f->dtype, lay.M);
-        kf<<<nchunks, kSeThreads, smem, st>>>(im, D, q, plan->d_taps, plan->ntaps, lay.chunks_per_img, nchunks,
+        kf<<<nchunks, kSeThreads, smem, st>>>(im, D, q, taps_dev, plan->ntaps, lay.chunks_per_img, nchunks,
                                               partial, grad_in);
         prof_end(ctx, st);
         ctx->launches += 1;
@@ -438,7 +467,7 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
         dim3 grid(static_cast<unsigned>((f->w + bx - 1) / bx), static_cast<unsigned>(std::min<long long>(rows, 65535)));
         prof_begin(ctx, st, "k_bwd_input");
         const BwdInputKernel kin = sgn > 0 ? input_kernel<1>(f->dtype) : input_kernel<-1>(f->dtype);
-        kin<<<grid, bx, 0, st>>>(im, D, q, plan->d_taps, plan->d_rows, plan->nrows, grad_in);
+        kin<<<grid, bx, 0, st>>>(im, D, q, taps_dev, plan->d_rows, plan->nrows, grad_in);
         prof_end(ctx, st);
         ctx->launches += 1;
         MORPH_CUDA_TRY(cudaGetLastError());
@@ -451,7 +480,7 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
             dim3 grid(nchunks, (plan->ntaps + kSeTaps - 1) / kSeTaps);
             prof_begin(ctx, st, "k_bwd_se_partial");
             const BwdSeKernel kse = sgn > 0 ? se_kernel<1>(f->dtype) : se_kernel<-1>(f->dtype);
-            kse<<<grid, kSeThreads, 0, st>>>(im, D, q, plan->d_taps, plan->ntaps, ch, nchunks, partial);
+            kse<<<grid, kSeThreads, 0, st>>>(im, D, q, taps_dev, plan->ntaps, ch, nchunks, partial);
             prof_end(ctx, st);
             ctx->launches += 1;
             MORPH_CUDA_TRY(cudaGetLastError());
@@ -459,7 +488,7 @@ static int backward_impl(morph_ctx* ctx, const morph_image* f, const morph_se* b
         MORPH_CUDA_TRY(cudaMemsetAsync(grad_se, 0, sizeof(float) * static_cast<size_t>(nbox), st));
         if (plan->ntaps > 0) {
             prof_begin(ctx, st, "k_bwd_se_final");
-            k_bwd_se_final<<<plan->ntaps, kFinalThreads, 0, st>>>(partial, nchunks, plan->d_taps, sgn, grad_se);
+            k_bwd_se_final<<<plan->ntaps, kFinalThreads, 0, st>>>(partial, nchunks, taps_dev, sgn, grad_se);
             prof_end(ctx, st);
             ctx->launches += 1;
             MORPH_CUDA_TRY(cudaGetLastError());
@@ -478,4 +507,31 @@ extern "C" int morph_erode_backward(morph_ctx* ctx, const morph_image* f, const 
                                     const int32_t* cE, const float* grad_out, float* grad_in, float* grad_se,
                                     morph_stream_t stream) {
     return backward_impl(ctx, f, b, E, cE, grad_out, grad_in, grad_se, stream, -1);
+}
+
+static morph_se host_view(const morph_se_dev* b) {
+    morph_se s;
+    s.kh = b->kh;
+    s.kw = b->kw;
+    s.oy = b->oy;
+    s.ox = b->ox;
+    s.mask = b->mask;
+    s.offset = nullptr;
+    return s;
+}
+
+extern "C" int morph_dilate_backward_dev_se(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b,
+                                            const int32_t* D, const int32_t* cD, const float* grad_out,
+                                            float* grad_in, float* grad_se, morph_stream_t stream) {
+    if (!b || !b->offset || b->max_offset < 0 || b->max_offset > 255) return MORPH_E_INVAL;
+    const morph_se s = host_view(b);
+    return backward_impl(ctx, f, &s, D, cD, grad_out, grad_in, grad_se, stream, +1, b->offset, b->max_offset);
+}
+
+extern "C" int morph_erode_backward_dev_se(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b,
+                                           const int32_t* E, const int32_t* cE, const float* grad_out,
+                                           float* grad_in, float* grad_se, morph_stream_t stream) {
+    if (!b || !b->offset || b->max_offset < 0 || b->max_offset > 255) return MORPH_E_INVAL;
+    const morph_se s = host_view(b);
+    return backward_impl(ctx, f, &s, E, cE, grad_out, grad_in, grad_se, stream, -1, b->offset, b->max_offset);
 }

@@ -521,6 +521,7 @@ __global__ void k_build_toeplitz(uint8_t* __restrict__ blocks, long long nbytes,
 DirectPlan::~DirectPlan() {
     if (d_toeplitz) cudaFree(d_toeplitz);
     if (d_meta) cudaFree(d_meta);
+    if (d_mask) cudaFree(d_mask);
 }
 
 // Host part of the plan: tiles, groups, passes, metadata and the issued FLOP.
@@ -531,10 +532,11 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     const bool dev = dev_bound >= 0;
     const int kh = se->kh, kw = se->kw;
     p->L = f->L;
-    // N = rows_n image rows x Lc levels: one 16-level chunk holds every level up to L = 16; above
-    // that a unit's level band usually spans few levels, and 8-level chunks of 32-row units
-    // contract about half as many levels as 16-level ones
-    p->Lc = f->L > kDirectLc ? kDirectLcBand : kDirectLc;
+    // N = rows_n image rows x Lc levels: one 16-level chunk holds every level up to L = 16; for
+    // 16 < L <= 64 a unit's level band usually spans under 16 levels, and 8-level chunks of
+    // 32-row units contract about half as many levels as 16-level ones; above that bands are
+    // wider (tens of levels) and 16-level chunks of 16-row units waste less
+    p->Lc = (f->L > kDirectLc && f->L <= 64) ? kDirectLcBand : kDirectLc;
     p->rows_n = kDirectN / p->Lc;
     p->kh = kh;
     p->kw = kw;
@@ -637,13 +639,16 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     p->meta.insert(p->meta.end(), rb.begin(), rb.end());
     p->meta.insert(p->meta.end(), gw.begin(), gw.end());
     p->meta.insert(p->meta.end(), rows.begin(), rows.end());
-    // taps of the per-unit lower bound on the top degree: the SE box cut into up to 16 x 16
-    // cells, from each the tap with the largest offset (ties: nearest the cell centre), plus
+    // taps of the per-unit lower bound on the top degree: the SE box cut into up to 16 x 16 cells
+    // (8 x 8 with 16-level chunks), from each the tap with the largest offset (ties: nearest
+    // the cell centre), plus
     // the origin when it is a tap (valid at every pixel of the image); stored as the source
     // displacement (oy - r, ox - c) and b
     p->band_tap_off = static_cast<int>(p->meta.size());
     {
-        const int ny = std::min(16, kh), nx = std::min(16, kw);
+        // the denser subset pays where 8-level chunks need a tight bound
+        const int cells = p->Lc == kDirectLcBand ? 16 : 8;
+        const int ny = std::min(cells, kh), nx = std::min(cells, kw);
         std::vector<int> bt;
         bool has_origin = false;
         for (int a = 0; a < ny; ++a)
@@ -723,6 +728,46 @@ int build_direct_plan(morph_ctx* ctx, const morph_image* f, const morph_se* se, 
                        CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
+// Plan of a device-resident SE: `se` holds the (reflected, for the erosion) mask
+// and no offsets, which lie in [0, bound] in device memory.  The plan keeps its
+// metadata and the mask on the device; the Toeplitz blocks depend on the
+// offsets and are written by every call (launch_toeplitz_dev).
+int build_direct_plan_dev(const morph_image* f, const morph_se* se, int bound, int erode, DirectPlan* p) {
+    int rc = plan_direct_host(f, se, erode, p, bound);
+    if (rc || p->taps == 0) return rc;
+    const size_t nbox = static_cast<size_t>(se->kh) * se->kw;
+    MORPH_CUDA_TRY(cudaMalloc(&p->d_meta, p->meta.size() * sizeof(int)));
+    MORPH_CUDA_TRY(cudaMemcpy(p->d_meta, p->meta.data(), p->meta.size() * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<uint8_t> m(nbox);
+    for (size_t t = 0; t < nbox; ++t) m[t] = se->mask[t] ? 1 : 0;
+    MORPH_CUDA_TRY(cudaMalloc(&p->d_mask, nbox));
+    MORPH_CUDA_TRY(cudaMemcpy(p->d_mask, m.data(), nbox, cudaMemcpyHostToDevice));
+    return MORPH_OK;
+}
+
+size_t direct_toeplitz_bytes(const DirectPlan& p) { return static_cast<size_t>(p.toeplitz_blocks) * 128 * 128; }
+
+// The Toeplitz blocks of a device-resident SE's plan into `blocks` (stream-ordered;
+// offsets outside [0, max b] raise the data error), and their tensor map.
+int launch_toeplitz_dev(morph_ctx* ctx, const DirectPlan& p, const int32_t* dev_off, int reflect, uint8_t* blocks,
+                        CUtensorMap* tmA, cudaStream_t st) {
+    const long long tb = static_cast<long long>(direct_toeplitz_bytes(p));
+    long long nblk = (tb + 255) / 256;
+    if (nblk > ctx->num_sms * 8LL) nblk = ctx->num_sms * 8LL;
+    if (nblk < 1) nblk = 1;
+    prof_begin(ctx, st, "k_build_toeplitz");
+    k_build_toeplitz<<<static_cast<unsigned>(nblk), 256, 0, st>>>(blocks, tb, p.d_mask, dev_off, p.d_meta, p.n_pass,
+                                                                 p.nk, p.J, p.G, p.kw, p.kh * p.kw, reflect, p.maxb,
+                                                                 ctx->d_err);
+    prof_end(ctx, st);
+    ctx->launches += 1;
+    MORPH_CUDA_TRY(cudaGetLastError());
+    const uint64_t dims[2] = {128, static_cast<uint64_t>(p.toeplitz_blocks) * 128};
+    const uint64_t strides[1] = {128};
+    const uint32_t box[2] = {128, 128};
+    return encode_tmap(tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, blocks, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
 void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,
                          int32_t* out_cnt, long long tile_base, int* status) {
     std::memset(static_cast<void*>(d), 0, sizeof(*d));
@@ -749,6 +794,8 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
     d->band_tap_off = p.band_tap_off;
     d->n_band_taps = p.n_band_taps;
     d->band = nullptr;
+    d->dev_off = nullptr;
+    d->dev_reflect = 0;
     d->rows_n = p.rows_n;
     d->J = p.J;
     d->G = p.G;
@@ -810,6 +857,16 @@ constexpr int kBandWinBytes = 96 * 1024;   // shared-memory window of a unit, 4 
 constexpr int kBandPairs = 8;              // pixel pairs per thread (32 rows x 128 columns / 2 / 256 threads)
 constexpr int kBandWMax = 1024;            // offsets above this are lowered to it for the bound (fp16-exact sums)
 
+// Offset of a lower-bound tap: stored in the plan, or (v < 0) the device-resident
+// offset of box entry -v - 1, clamped into [0, max b] (an offset outside it is
+// reported by the Toeplitz build as a data error).
+__device__ __forceinline__ int band_tap_offset(const DirectProblemDev* P, int v) {
+    if (v >= 0) return v;
+    const int t = -v - 1;
+    const int o = P->dev_off[P->dev_reflect ? P->kh * P->kw - 1 - t : t];
+    return min(max(o, 0), P->maxb);
+}
+
 // Level of pixel (i, j), flipped for the erosion and clamped into [0, L).
 __device__ __forceinline__ int band_level(const DirectProblemDev* P, long long ibase, int i, int j) {
     int v = band_pixel(P->src, P->dtype, ibase + static_cast<long long>(i) * P->row_stride + j);
@@ -820,6 +877,8 @@ __device__ __forceinline__ int band_level(const DirectProblemDev* P, long long i
 // Warp `warp` stages window rows rr = warp, warp + nwarp, ...: its (row, 32-column
 // group) items are taken eight at a time, so each lane has eight loads in flight
 // before it stores their levels (the staging is bound by load latency otherwise).
+constexpr int kBandStageBatch = 6;         // staging loads in flight per lane
+
 template <typename Pix>
 __device__ __forceinline__ int band_stage_rows(const DirectProblemDev* P, long long ibase, int wr0, int wc0, int WR,
                                                int WC, __half* qh, int warp, int nwarp, int lane) {
@@ -829,15 +888,16 @@ __device__ __forceinline__ int band_stage_rows(const DirectProblemDev* P, long l
     const int my_rows = warp < WR ? (WR - warp + nwarp - 1) / nwarp : 0;
     const int items = my_rows * ng;
     int hi = -1;
-    for (int base = 0; base < items; base += 8) {
-        int v[8], rr[8], cc[8];
-        bool in[8];
+    for (int base = 0; base < items; base += kBandStageBatch) {
+        int v[kBandStageBatch], e[kBandStageBatch], cc[kBandStageBatch];
+        bool in[kBandStageBatch];
         int r = base / ng, gcol = base - r * ng;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            rr[k] = warp + r * nwarp;
+        for (int k = 0; k < kBandStageBatch; ++k) {
+            const int rr = warp + r * nwarp;
             cc[k] = gcol * 32 + lane;
-            const int i = wr0 + rr[k], j = wc0 + cc[k];
+            e[k] = rr * WC + cc[k];
+            const int i = wr0 + rr, j = wc0 + cc[k];
             in[k] = base + k < items && cc[k] < WC && i >= 0 && i < h && j >= 0 && j < w;
             v[k] = in[k] ? static_cast<int>(src[ibase + static_cast<long long>(i) * P->row_stride + j]) : 0;
             if (++gcol == ng) {
@@ -846,7 +906,7 @@ __device__ __forceinline__ int band_stage_rows(const DirectProblemDev* P, long l
             }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kBandStageBatch; ++k) {
             if (base + k >= items || cc[k] >= WC) continue;
             float fv = -4096.f;
             if (in[k]) {
@@ -856,16 +916,63 @@ __device__ __forceinline__ int band_stage_rows(const DirectProblemDev* P, long l
                 fv = static_cast<float>(lv);
             }
             const __half hv = __float2half_rn(fv);
-            const int e = rr[k] * WC + cc[k];
-            qh[2 * e] = hv;                                        // low half of pair cc
-            if (cc[k] > 0) qh[2 * e - 1] = hv;                     // high half of pair cc - 1
-            if (cc[k] == WC - 1) qh[2 * e + 1] = __float2half_rn(-4096.f);   // the row's last pair
+            qh[2 * e[k]] = hv;                                     // low half of pair cc
+            if (cc[k] > 0) qh[2 * e[k] - 1] = hv;                  // high half of pair cc - 1
+            if (cc[k] == WC - 1) qh[2 * e[k] + 1] = __float2half_rn(-4096.f);   // the row's last pair
         }
     }
     return hi;
 }
 
-__global__ void __launch_bounds__(256) k_band(const __grid_constant__ DirectLaunch dl) {
+// The thread's minimum over its NP pixel pairs of the subset maximum: pair k of
+// thread t is pair t + 256 k of the unit, row-major (uw / 2 pairs per row).
+// Two accumulators per pair take alternate taps, so consecutive taps do not
+// wait on each other.
+template <int NP>
+__device__ __forceinline__ int band_lower(const DirectProblemDev* P, const TileCoord& tc, const __half2* q,
+                                          const int* s_toff, const __half2* s_tw, int ntap, int WC, int npair) {
+    const int uw = P->T * P->J, half_w = uw >> 1, sh = __ffs(half_w) - 1;
+    if (static_cast<int>(threadIdx.x) >= npair) return 0x7fffffff;   // (NP == 1 with fewer pairs than threads)
+    __half2 a0[NP], a1[NP];
+    int base[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        a0[k] = __floats2half2_rn(-1.f, -1.f);
+        a1[k] = a0[k];
+        const int pp = threadIdx.x + k * 256;
+        const int pr = pp >> sh, pc = 2 * (pp & (half_w - 1));
+        base[k] = (pr + P->kh - 1 - P->oy) * WC + pc + P->kw - 1 - P->ox;
+    }
+    int s = 0;
+    for (; s + 1 < ntap; s += 2) {
+        const int o0 = s_toff[s], o1 = s_toff[s + 1];
+        const __half2 w0 = s_tw[s], w1 = s_tw[s + 1];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            a0[k] = __hmax2(a0[k], __hadd2(q[base[k] + o0], w0));
+            a1[k] = __hmax2(a1[k], __hadd2(q[base[k] + o1], w1));
+        }
+    }
+    if (s < ntap) {
+        const int o0 = s_toff[s];
+        const __half2 w0 = s_tw[s];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) a0[k] = __hmax2(a0[k], __hadd2(q[base[k] + o0], w0));
+    }
+    int lb = 0x7fffffff;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int pp = threadIdx.x + k * 256;
+        const int i = tc.i0 + (pp >> sh), j = tc.j0 + 2 * (pp & (half_w - 1));
+        if (i >= P->h) continue;
+        const float2 m = __half22float2(__hmax2(a0[k], a1[k]));
+        if (j >= 0 && j < P->w) lb = min(lb, static_cast<int>(m.x));
+        if (j + 1 >= 0 && j + 1 < P->w) lb = min(lb, static_cast<int>(m.y));
+    }
+    return lb;
+}
+
+__global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectLaunch dl, int win_bytes) {
     // The unit's input window (rows i - r + oy, columns j - c + ox over the SE box, not
     // clipped) as overlapping half2 pairs q[r][k] = (level(r, k), level(r, k + 1)), -4096
     // outside the image; a pixel pair (j, j + 1) reads a tap's two sources with one load.
@@ -885,13 +992,13 @@ __global__ void __launch_bounds__(256) k_band(const __grid_constant__ DirectLaun
         const long long ibase = static_cast<long long>(tc.n) * P->batch_stride;
         const int wr0 = tc.i0 - (P->kh - 1 - P->oy), wc0 = tc.j0 - (P->kw - 1 - P->ox);
         const int WR = P->rows_n + P->kh - 1, WC = uw + P->kw;   // one spare column for the pairs
-        const bool fast = static_cast<long long>(WR) * WC * 4 <= kBandWinBytes &&
+        const bool fast = static_cast<long long>(WR) * WC * 4 <= win_bytes &&
                           P->rows_n * (uw >> 1) <= 256 * kBandPairs;      // block-uniform
         __syncthreads();   // the previous unit's readers of the shared arrays are done
         for (int k = threadIdx.x; k < ntap; k += blockDim.x) {
             const int* tp = P->meta + P->band_tap_off + 3 * k;
             s_toff[k] = tp[0] * WC + tp[1];
-            const float wv = static_cast<float>(min(tp[2], kBandWMax));
+            const float wv = static_cast<float>(min(band_tap_offset(P, tp[2]), kBandWMax));
             s_tw[k] = __floats2half2_rn(wv, wv);
         }
         int hi = -1;
@@ -904,35 +1011,13 @@ __global__ void __launch_bounds__(256) k_band(const __grid_constant__ DirectLaun
             else
                 hi = band_stage_rows<int32_t>(P, ibase, wr0, wc0, WR, WC, qh, warp, nwarp, lane);
             __syncthreads();
-            // pixel pairs of the unit: rows_n rows x uw / 2 pairs per row, kBandPairs per thread
-            const int half_w = uw >> 1, sh = __ffs(half_w) - 1;
-            const int npair = P->rows_n * half_w;
-            __half2 acc[kBandPairs];
-            int base[kBandPairs];
-#pragma unroll
-            for (int k = 0; k < kBandPairs; ++k) {
-                acc[k] = __floats2half2_rn(-1.f, -1.f);
-                const int pp = threadIdx.x + k * 256;
-                const int pr = pp >> sh, pc = 2 * (pp & (half_w - 1));
-                base[k] = (pr + P->kh - 1 - P->oy) * WC + pc + P->kw - 1 - P->ox;
-            }
-            for (int s = 0; s < ntap; ++s) {
-                const int off = s_toff[s];
-                const __half2 tw = s_tw[s];
-#pragma unroll
-                for (int k = 0; k < kBandPairs; ++k)
-                    if (threadIdx.x + k * 256 < npair) acc[k] = __hmax2(acc[k], __hadd2(q[base[k] + off], tw));
-            }
-#pragma unroll
-            for (int k = 0; k < kBandPairs; ++k) {
-                const int pp = threadIdx.x + k * 256;
-                if (pp >= npair) continue;
-                const int i = tc.i0 + (pp >> sh), j = tc.j0 + 2 * (pp & (half_w - 1));
-                if (i >= h) continue;
-                const float2 m = __half22float2(acc[k]);
-                if (j >= 0 && j < w) lb = min(lb, static_cast<int>(m.x));
-                if (j + 1 >= 0 && j + 1 < w) lb = min(lb, static_cast<int>(m.y));
-            }
+            // pixel pairs of the unit: rows_n rows x uw / 2 pairs per row, npair / 256 per thread
+            // (a power of two; with fewer pairs than threads, one pair for the first npair threads)
+            const int npair = P->rows_n * (uw >> 1);
+            if (npair <= 256) lb = band_lower<1>(P, tc, q, s_toff, s_tw, ntap, WC, npair);
+            else if (npair <= 512) lb = band_lower<2>(P, tc, q, s_toff, s_tw, ntap, WC, npair);
+            else if (npair <= 1024) lb = band_lower<4>(P, tc, q, s_toff, s_tw, ntap, WC, npair);
+            else lb = band_lower<8>(P, tc, q, s_toff, s_tw, ntap, WC, npair);
         } else {
             // windows too large for shared memory (SE boxes of hundreds of rows): direct loads
             const int r0 = max(0, wr0), r1 = min(h, tc.i0 + P->rows_n + P->oy);
@@ -950,7 +1035,7 @@ __global__ void __launch_bounds__(256) k_band(const __grid_constant__ DirectLaun
                         const int si = i + tp[0], sj = j + tp[1];
                         if (static_cast<unsigned>(si) < static_cast<unsigned>(h) &&
                             static_cast<unsigned>(sj) < static_cast<unsigned>(w))
-                            m = max(m, band_level(P, ibase, si, sj) + min(tp[2], kBandWMax));
+                            m = max(m, band_level(P, ibase, si, sj) + min(band_tap_offset(P, tp[2]), kBandWMax));
                     }
                     lb = min(lb, m);
                 }
@@ -980,19 +1065,28 @@ __global__ void __launch_bounds__(256) k_band(const __grid_constant__ DirectLaun
     }
 }
 
-int launch_band(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st) {
+int direct_band_window(const DirectProblemDev& d) {
+    if (d.band == nullptr) return 0;
+    const long long b = static_cast<long long>(d.rows_n + d.kh - 1) * (d.T * d.J + d.kw) * 4;
+    return static_cast<int>(std::min<long long>(kBandWinBytes, (b + 1023) & ~1023LL));
+}
+
+int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, cudaStream_t st) {
     if (dl.total_tiles <= 0) return MORPH_OK;
     bool any = dl.many != nullptr || dl.single.band != nullptr;
     if (!any) return MORPH_OK;
+    win_bytes = std::max(1024, std::min(win_bytes, kBandWinBytes));
+    // resident CTAs per SM: 8 by threads, fewer when their windows fill shared memory
+    const long long per_sm = std::max(1, std::min(8, (220 * 1024) / (win_bytes + 3 * 1024)));
     long long grid = dl.total_tiles;
-    const long long cap = static_cast<long long>(ctx->num_sms) * 2;   // 96 KB of shared memory each
+    const long long cap = static_cast<long long>(ctx->num_sms) * per_sm;
     if (grid > cap) grid = cap;
     prof_begin(ctx, st, "k_band");
     if (!kernels_ready(ctx->device, kGroupBand)) {
         MORPH_CUDA_TRY(cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandWinBytes));
         mark_kernels_ready(ctx->device, kGroupBand);
     }
-    k_band<<<static_cast<unsigned>(grid), 256, kBandWinBytes, st>>>(dl);
+    k_band<<<static_cast<unsigned>(grid), 256, win_bytes, st>>>(dl, win_bytes);
     prof_end(ctx, st);
     ctx->launches += 1;
     MORPH_CUDA_TRY(cudaGetLastError());

@@ -177,6 +177,17 @@ static int inval(const char* why) {
     return MORPH_E_INVAL;
 }
 
+static int validate_image(const morph_image* f) {
+    if (!f) return inval("null image");
+    if (!f->data) return inval("null image data");
+    if (f->dtype < MORPH_U8 || f->dtype > MORPH_I32) return inval("dtype");
+    if (f->n < 1 || f->h < 1 || f->w < 1) return inval("image shape");
+    if (f->L < 2 || f->L > 256) return inval("L outside [2, 256]");
+    if (f->row_stride < f->w) return inval("row_stride < w");
+    if (f->batch_stride < static_cast<int64_t>(f->h - 1) * f->row_stride + f->w) return inval("batch_stride");
+    return MORPH_OK;
+}
+
 static int validate(const morph_image* f, const morph_se* b) {
     if (!f || !b) return inval("null image or SE");
     if (!f->data) return inval("null image data");
@@ -501,7 +512,100 @@ static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int er
     dl.err = ctx->d_err;
     dl.mma_count = ctx->d_mma;
     dl.wait_ns = ctx->wait_ns;
-    rc = launch_band(ctx, dl, st);
+    rc = launch_band(ctx, dl, direct_band_window(dl.single), st);
+    if (rc) return rc;
+    return launch_direct(ctx, dl, st);
+}
+
+// One dilation / erosion by an SE with device-resident offsets (FP8 route).
+// The plan depends on the mask, the bound and the shape only; each call writes
+// the SE's Toeplitz blocks from the device offsets into the workspace.
+int run_one_dev(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b, int erode, int32_t* out, int32_t* cnt,
+                cudaStream_t st) {
+    if (!ctx) return inval("null context");
+    if (!out) return inval("null output");
+    int rc = validate_image(f);
+    if (rc) return rc;
+    if (!b || !b->mask || !b->offset) return inval("null SE, mask or offsets");
+    if (b->kh < 1 || b->kw < 1 || b->kh > 512 || b->kw > 512) return inval("SE box outside 1..512");
+    if (b->oy < -4096 || b->oy > 4096 || b->ox < -4096 || b->ox > 4096) return inval("SE origin");
+    if (b->max_offset < 0 || b->max_offset > 255) return inval("max_offset outside [0, 255]");
+    const int kh = b->kh, kw = b->kw;
+    std::vector<uint8_t> mask(static_cast<size_t>(kh) * kw);
+    for (int r = 0; r < kh; ++r)
+        for (int c = 0; c < kw; ++c)
+            mask[r * kw + c] = b->mask[erode ? (kh - 1 - r) * kw + (kw - 1 - c) : r * kw + c] ? 1 : 0;
+    morph_se e;
+    e.kh = kh;
+    e.kw = kw;
+    e.oy = erode ? kh - 1 - b->oy : b->oy;
+    e.ox = erode ? kw - 1 - b->ox : b->ox;
+    e.mask = mask.data();
+    e.offset = nullptr;
+    char head[160];
+    std::snprintf(head, sizeof(head), "dev|e%d|L%d|n%d|h%d|w%d|k%dx%d|o%d,%d|b%d|", erode, f->L, f->n, f->h, f->w, kh,
+                  kw, e.oy, e.ox, b->max_offset);
+    std::string key = head;
+    key.append(reinterpret_cast<const char*>(mask.data()), mask.size());
+    std::shared_ptr<Plan> plan;
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        it->second->last_use = ++ctx->plan_tick;
+        plan = it->second;
+    } else {
+        plan = std::make_shared<Plan>();
+        plan->route = ROUTE_DIRECT;
+        rc = build_direct_plan_dev(f, &e, b->max_offset, erode, &plan->direct);
+        if (rc) return rc;
+        if (plan->direct.taps == 0) plan->route = ROUTE_EMPTY;
+        plan->dev_bytes = plan->direct.meta.size() * sizeof(int) + mask.size();
+        plan->last_use = ++ctx->plan_tick;
+        ctx->plan_bytes += plan->dev_bytes;
+        ctx->plans.emplace(key, plan);
+    }
+    const long long npx = static_cast<long long>(f->n) * f->h * f->w;
+    if (plan->route == ROUTE_EMPTY) return launch_fill_empty(ctx, out, cnt, npx, erode ? f->L - 1 : 0, st);
+    const DirectPlan& dp = plan->direct;
+    const size_t toe_off = (direct_ws_bytes(f) + 1023) & ~size_t(1023);
+    void* ws = nullptr;
+    rc = ctx_workspace(ctx, toe_off + direct_toeplitz_bytes(dp), &ws);
+    if (rc) return rc;
+    uint8_t* planes = static_cast<uint8_t*>(ws);
+    DirectBand* band = reinterpret_cast<DirectBand*>(planes + planes_bytes(f));
+    CUtensorMap tmA;
+    rc = launch_toeplitz_dev(ctx, dp, b->offset, erode, planes + toe_off, &tmA, st);
+    if (rc) return rc;
+    EncodeJob job;
+    job.src = f->data;
+    job.dtype = f->dtype;
+    job.n = f->n;
+    job.h = f->h;
+    job.w = f->w;
+    job.row_stride = f->row_stride;
+    job.batch_stride = f->batch_stride;
+    job.L = f->L;
+    job.flip = erode;
+    job.planes = planes;
+    job.w_pad = dp.w_pad;
+    job.shift = dp.shift;
+    job.item_base = 0;
+    rc = launch_encode(ctx, &job, 1, static_cast<long long>(f->n) * f->h * (dp.w_pad / 16), nullptr, st);
+    if (rc) return rc;
+    DirectLaunch dl;
+    std::memset(static_cast<void*>(&dl), 0, sizeof(dl));
+    direct_fill_problem(dp, &dl.single, planes, out, cnt, 0, &rc);
+    if (rc) return rc;
+    dl.single.tmA = tmA;
+    direct_fill_band(&dl.single, f, band);
+    dl.single.dev_off = b->offset;
+    dl.single.dev_reflect = erode;
+    dl.many = nullptr;
+    dl.nprob = 1;
+    dl.total_tiles = dp.tiles;
+    dl.err = ctx->d_err;
+    dl.mma_count = ctx->d_mma;
+    dl.wait_ns = ctx->wait_ns;
+    rc = launch_band(ctx, dl, direct_band_window(dl.single), st);
     if (rc) return rc;
     return launch_direct(ctx, dl, st);
 }
@@ -511,6 +615,16 @@ static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int er
 using namespace morph;
 
 extern "C" {
+
+int morph_dilate_dev_se(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b, int32_t* out,
+                        int32_t* out_count, morph_stream_t stream) {
+    return run_one_dev(ctx, f, b, 0, out, out_count, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int morph_erode_dev_se(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b, int32_t* out,
+                       int32_t* out_count, morph_stream_t stream) {
+    return run_one_dev(ctx, f, b, 1, out, out_count, reinterpret_cast<cudaStream_t>(stream));
+}
 
 int morph_ctx_create(int device, morph_ctx** out) {
     if (!out) return MORPH_E_INVAL;

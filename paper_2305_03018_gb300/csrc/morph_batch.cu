@@ -225,7 +225,9 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
         int kind = b->probs.empty() ? 0 : direct_kind(b->probs[0]);
         for (const auto& d : b->probs)
             if (direct_kind(d) != kind) kind = 0;
-        rc = launch_band(ctx, dl, st);
+        int win = 0;
+        for (const auto& d : b->probs) win = std::max(win, direct_band_window(d));
+        rc = launch_band(ctx, dl, win, st);
         if (rc) return rc;
         rc = launch_direct(ctx, dl, st, kind);
         if (rc) return rc;

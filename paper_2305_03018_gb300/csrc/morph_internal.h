@@ -58,8 +58,8 @@ constexpr int kDirectMaxPasses = 32;
 constexpr long long kDirectSplitMinUnits = 2 * 152;   // split two-tile units only with two waves on 152 SMs
 constexpr int kDirectN = 256;        // MMA N: image rows x grey levels of one chunk
 constexpr int kDirectM = 128;        // MMA M: offset groups x output columns
-constexpr int kDirectLc = 16;        // grey levels per chunk of the N axis when L <= 16 (16 image rows)
-constexpr int kDirectLcBand = 8;     // ... when L > 16 and the unit's level band is computed (32 image rows)
+constexpr int kDirectLc = 16;        // grey levels per chunk of the N axis when L <= 16 or L > 64 (16 image rows)
+constexpr int kDirectLcBand = 8;     // ... when 16 < L <= 64 (32 image rows)
 constexpr int kBandTapsMax = 264;    // taps of the per-unit lower bound on the top degree (16 x 16 cells + origin)
 
 // Per unit of a direct launch: hi = the largest level in the unit's input
@@ -83,6 +83,8 @@ struct DirectProblemDev {
     const int32_t* out_sub;
     const int* meta;        // pass_row_begin[n_pass+1], group_w[n_pass*8], rows[...], band taps (3 ints each)
     const DirectBand* band; // per unit; nullptr: every level, ceil(L / Lc) chunks
+    const int32_t* dev_off; // device-resident SE offsets (box order of the caller's SE), or nullptr
+    int dev_reflect;        // 1: read dev_off at kh kw - 1 - t (the erosion's reflected SE)
     const void* src;        // the image (read by the band kernel)
     int dtype;
     long long row_stride, batch_stride;
@@ -122,6 +124,7 @@ struct DirectPlan {
     std::vector<int> meta;
     uint8_t* d_toeplitz = nullptr;
     int* d_meta = nullptr;
+    uint8_t* d_mask = nullptr;        // device-resident-SE plans: the (reflected) mask for the per-call Toeplitz build
     long long toeplitz_blocks = 0;
     CUtensorMap tmA;
     double issued_flop = 0;           // dense MMA FLOP per launch with every level (ceil(L / Lc) chunks)
@@ -277,12 +280,21 @@ int direct_smem_bytes(int stages);
 int direct_stages();
 void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,
                          int32_t* out_cnt, long long tile_base, int* status);
+// device-resident SE offsets: plan (metadata and mask on the device), the per-call Toeplitz
+// blocks and their size
+int build_direct_plan_dev(const morph_image* f, const morph_se* se, int bound, int erode, DirectPlan* p);
+size_t direct_toeplitz_bytes(const DirectPlan& p);
+int launch_toeplitz_dev(morph_ctx* ctx, const DirectPlan& p, const int32_t* dev_off, int reflect, uint8_t* blocks,
+                        CUtensorMap* tmA, cudaStream_t st);
 // the image and the per-unit band buffer of a problem (band may be nullptr: every level)
 void direct_fill_band(DirectProblemDev* d, const morph_image* f, DirectBand* band);
 // bytes of the per-unit band buffer for an image of this shape (any plan)
 size_t direct_band_bytes(const morph_image* f);
-// per-unit grey-level bands of every problem of a direct launch (before launch_direct, same stream)
-int launch_band(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st);
+// per-unit grey-level bands of every problem of a direct launch (before launch_direct, same
+// stream); win_bytes: shared memory per CTA for the unit windows (the largest
+// direct_band_window of the launch's problems; larger windows take a slower path)
+int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, cudaStream_t st);
+int direct_band_window(const DirectProblemDev& d);
 int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st,
                       const OutAdjust* adj = nullptr);
 // validation, erosion reflection, route choice and (cached) plan of one problem

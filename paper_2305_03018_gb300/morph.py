@@ -39,6 +39,11 @@ class morph_se(ctypes.Structure):
                 ("mask", ctypes.POINTER(ctypes.c_uint8)), ("offset", ctypes.POINTER(ctypes.c_int32))]
 
 
+class morph_se_dev(ctypes.Structure):
+    _fields_ = [("kh", ctypes.c_int), ("kw", ctypes.c_int), ("oy", ctypes.c_int), ("ox", ctypes.c_int),
+                ("mask", ctypes.POINTER(ctypes.c_uint8)), ("offset", ctypes.c_void_p), ("max_offset", ctypes.c_int)]
+
+
 class morph_volume(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int), ("n", ctypes.c_int), ("d", ctypes.c_int),
                 ("h", ctypes.c_int), ("w", ctypes.c_int), ("row_stride", ctypes.c_int64),
@@ -99,6 +104,12 @@ _SIGS = {
                                              _P, _P, _P]),
     "morph_erode_backward": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), _P, _P, _P,
                                             _P, _P, _P]),
+    "morph_dilate_dev_se": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se_dev), _P, _P, _P]),
+    "morph_erode_dev_se": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se_dev), _P, _P, _P]),
+    "morph_dilate_backward_dev_se": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se_dev),
+                                                    _P, _P, _P, _P, _P, _P]),
+    "morph_erode_backward_dev_se": (ctypes.c_int, [_P, ctypes.POINTER(morph_image), ctypes.POINTER(morph_se_dev),
+                                                   _P, _P, _P, _P, _P, _P]),
     "morph_run_batch": (ctypes.c_int, [_P, ctypes.POINTER(morph_problem), ctypes.c_int, ctypes.POINTER(morph_opts),
                                        _P]),
     "morph_batch_capture": (ctypes.c_int, [_P, ctypes.POINTER(morph_problem), ctypes.c_int,
@@ -275,6 +286,24 @@ def morph_launch_count(ctx) -> int:
     return int(load_library().morph_launch_count(ctx))
 
 
+def morph_dilate_dev_se(ctx, image, se, out_ptr, cnt_ptr, stream) -> int:
+    return load_library().morph_dilate_dev_se(ctx, ctypes.byref(image), ctypes.byref(se), out_ptr, cnt_ptr, stream)
+
+
+def morph_erode_dev_se(ctx, image, se, out_ptr, cnt_ptr, stream) -> int:
+    return load_library().morph_erode_dev_se(ctx, ctypes.byref(image), ctypes.byref(se), out_ptr, cnt_ptr, stream)
+
+
+def morph_dilate_backward_dev_se(ctx, image, se, d_ptr, cd_ptr, g_ptr, gin_ptr, gse_ptr, stream) -> int:
+    return load_library().morph_dilate_backward_dev_se(ctx, ctypes.byref(image), ctypes.byref(se), d_ptr, cd_ptr,
+                                                       g_ptr, gin_ptr, gse_ptr, stream)
+
+
+def morph_erode_backward_dev_se(ctx, image, se, e_ptr, ce_ptr, g_ptr, gin_ptr, gse_ptr, stream) -> int:
+    return load_library().morph_erode_backward_dev_se(ctx, ctypes.byref(image), ctypes.byref(se), e_ptr, ce_ptr,
+                                                      g_ptr, gin_ptr, gse_ptr, stream)
+
+
 def morph_ctx_set_wait_limit(ctx, ns: int) -> int:
     return load_library().morph_ctx_set_wait_limit(ctx, int(ns))
 
@@ -383,6 +412,25 @@ class SEView:
         self.c.offset = self.offset.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
 
 
+class SEDevView:
+    """An SE whose offsets are a CUDA int32 tensor [kh, kw] (a learnable layer's
+    parameter); the host mask is kept alive next to the C struct."""
+
+    def __init__(self, mask, offset_t, origin, max_offset: int):
+        self.mask = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        if offset_t.dtype != __import__("torch").int32 or not offset_t.is_cuda or not offset_t.is_contiguous():
+            raise ValueError("device offsets must be a contiguous CUDA int32 tensor")
+        if tuple(offset_t.shape) != self.mask.shape:
+            raise ValueError("mask and offsets must have one shape [kh, kw]")
+        self.offset_t = offset_t
+        self.c = morph_se_dev()
+        self.c.kh, self.c.kw = (int(s) for s in self.mask.shape)
+        self.c.oy, self.c.ox = int(origin[0]), int(origin[1])
+        self.c.mask = self.mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        self.c.offset = offset_t.data_ptr()
+        self.c.max_offset = int(max_offset)
+
+
 def se_view(se) -> SEView:
     """Accepts a workloads.SE-like object (mask, offset, origin) or a tuple."""
     if isinstance(se, SEView):
@@ -450,6 +498,21 @@ class Context:
 
     def erode(self, f, L, se, method="auto", count=False, stream=None, **kw):
         return self._run(1, f, L, se, method, count, stream, **kw)
+
+    def morph_dev_se(self, op, f, L, sev, count=False, stream=None, out=None, out_count=None):
+        """Dilation (op 0) or erosion (op 1) by an SEDevView (FP8 route, no host copy of the offsets)."""
+        import torch
+        img = make_image(f, L)
+        shape = (img.n, img.h, img.w)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.int32, device=f.device)
+        if count and out_count is None:
+            out_count = torch.empty(shape, dtype=torch.int32, device=f.device)
+        st = stream if stream is not None else current_stream_handle(f.device)
+        fn = morph_dilate_dev_se if op == 0 else morph_erode_dev_se
+        check(fn(self.handle, img, sev.c, out.data_ptr(), out_count.data_ptr() if count else None, st),
+              "morph_dilate_dev_se" if op == 0 else "morph_erode_dev_se")
+        return (out, out_count) if count else out
 
     def _run3d(self, op, f, L, mask, offset, origin, method, count, stream):
         import torch
