@@ -344,6 +344,14 @@ int morph_ctx_set_wait_limit(morph_ctx *ctx, uint64_t ns);
  * Synchronises the device; *out receives the count. */
 int morph_mma_count(morph_ctx *ctx, uint64_t *out);
 
+/* Multiply-adds of the contraction the FP8 route's units needed -- for each
+ * unit and offset-group pass, the pass's taps x the grey levels of its band x
+ * the unit's pixels (Step 2 restricted to the degrees Step 3 can read) --
+ * summed on the device by the band kernel over the calls through this context
+ * (host-resident SEs with L > 16; a measurement hook, the method's own work
+ * for the roofline).  Synchronises the device; *out receives the sum. */
+int morph_band_work(morph_ctx *ctx, uint64_t *out);
+
 /* Per-kernel device time, summed over the launches recorded while profiling
  * was on. */
 typedef struct {

@@ -60,8 +60,8 @@ constexpr int kStages = 3;
 constexpr int kStageA = 128 * 128;             // 16 KB: 128 Toeplitz rows x 128 B of K
 constexpr int kStageB = kDirectN * 128;        // 32 KB: 256 (row, level) rows x 128 B of K
 constexpr int kStageBytes = kStageA + kStageB;
-constexpr int kRedEntries = 32 * 128;          // rows_n (<= 32) x 128 lanes; with 16 rows, both tiles of a
-                                               // two-tile unit are read out before either is reduced
+constexpr int kRedEntries = 2 * 32 * 128;      // two tiles x rows_n (<= 32) x 128 lanes, 4 B each: both tiles
+                                               // of a two-tile unit are read out before either is reduced
 constexpr int kRunEntries = 4096;              // rows_n x J x T (<= 4096: 32 x 128, or 16 x 128 x 2)
 constexpr int kDirectThreads = 192;
 constexpr uint32_t kTmemCols = 2 * kDirectN;   // two accumulators
@@ -78,7 +78,7 @@ struct DirectSmemTail {
 
 int direct_stages() { return kStages; }
 int direct_smem_bytes(int stages) {
-    return 1024 + stages * kStageBytes + (kRedEntries + kRunEntries) * 8 + static_cast<int>(sizeof(DirectSmemTail));
+    return 1024 + stages * kStageBytes + kRedEntries * 4 + kRunEntries * 8 + static_cast<int>(sizeof(DirectSmemTail));
 }
 
 __device__ __forceinline__ const DirectProblemDev* direct_find(const DirectLaunch& dl, long long t) {
@@ -147,8 +147,10 @@ template <int TT>
 __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_constant__ DirectLaunch dl) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    int2* red = reinterpret_cast<int2*>(base + kStages * kStageBytes);
-    int2* run = red + kRedEntries;
+    // red: one lane's result of one image row of one chunk, (top level in the chunk + 1) << 20 |
+    // its count (0: no level set; counts <= |B| <= 512^2 < 2^20); run: (degree, count) so far
+    uint32_t* red = reinterpret_cast<uint32_t*>(base + kStages * kStageBytes);
+    int2* run = reinterpret_cast<int2*>(red + kRedEntries);
     DirectSmemTail* tail = reinterpret_cast<DirectSmemTail*>(run + kRunEntries);
     volatile int* abort_flag = &tail->abort;
     const unsigned long long wait_ns = dl.wait_ns != 0ull ? dl.wait_ns : kWaitLimitNs;
@@ -350,7 +352,6 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
             const DirectProblemDev* P = direct_find(dl, t);
             const TileCoord tc = direct_tile(P, t);
             const int J = P->J, G = P->G, rows_n = P->rows_n, Lc = P->Lc, T = (TT == 0) ? P->T : (TT == 3 ? 2 : TT);
-            const int g = m / J;
             const int* gw = P->meta + (P->n_pass + 1);
             const DirectBand bd = direct_band(P, t);
             int n_units = 0;                              // accumulations of this unit, all passes
@@ -372,17 +373,21 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                     ok = mbar_wait(smem_u32(&tail->tfull[1]), use1 & 1u, abort_flag, dl.err, wait_ns);
                 if (epi_any_failed(!ok)) { failed = true; break; }
                 tc_fence_after();
-                const int wg = ((g < G) ? gw[p * 8 + g] : 0) + lev0;   // degree of the chunk's level 0 in group g
-                // (max, sum-at-max) over the groups of tile tt, merged with the earlier unit passes
+                // (max, sum-at-max) over the groups of tile tt, merged with the earlier unit passes;
+                // group gg's degree of the chunk's level k is lev0 + k + its offset
                 const int pairs = rows_n * J;
+                const int* gwp = gw + p * 8;
                 auto reduce = [&](int tt, int rbase) {
                     for (int idx = et; idx < pairs; idx += 128) {
                         const int tr = idx / J, jl = idx - tr * J;
                         int best = -1, bc = 0;
                         for (int gg = 0; gg < G; ++gg) {
-                            const int2 e = red[rbase + tr * 128 + gg * J + jl];
-                            if (e.x > best) { best = e.x; bc = e.y; }
-                            else if (e.x == best && e.x >= 0) bc += e.y;
+                            const uint32_t e = red[rbase + tr * 128 + gg * J + jl];
+                            if (e == 0u) continue;
+                            const int deg = lev0 + static_cast<int>(e >> 20) - 1 + gwp[gg];
+                            const int c = static_cast<int>(e & 0xFFFFFu);
+                            if (deg > best) { best = deg; bc = c; }
+                            else if (deg == best) bc += c;
                         }
                         int2 cur = make_int2(best, bc);
                         const int ri = tt * pairs + idx;
@@ -422,28 +427,17 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
 #pragma unroll
                             for (int k = 0; k < 8; ++k)
                                 if (v[k] > 0.5f) { top = k; cnt = v[k]; }
-                        } else if (Lc == 16) {
+                        } else {                                  // Lc == 16
                             float v[16];
                             tmem_ld_32x32b_x16(trow + col0, v);
                             tc_wait_ld();
 #pragma unroll
                             for (int k = 0; k < 16; ++k)
                                 if (v[k] > 0.5f) { top = k; cnt = v[k]; }
-                        } else {
-                            for (int c = Lc / 32 - 1; c >= 0; --c) {
-                                if (__all_sync(0xffffffffu, top >= 0)) break;
-                                float v[32];
-                                tmem_ld_32x32b_x32(trow + col0 + 32u * c, v);
-                                tc_wait_ld();
-                                if (top < 0) {
-#pragma unroll
-                                    for (int k = 0; k < 32; ++k)
-                                        if (v[k] > 0.5f) { top = 32 * c + k; cnt = v[k]; }
-                                }
-                            }
                         }
                         red[rbase + tr * 128 + m] =
-                            (top >= 0) ? make_int2(top + wg, __float2int_rn(cnt)) : make_int2(-1, 0);
+                            (top >= 0) ? (static_cast<uint32_t>(top + 1) << 20) | static_cast<uint32_t>(__float2int_rn(cnt))
+                                       : 0u;
                     }
                     // this accumulator's TMEM reads are done: hand it back
                     tc_fence_before();
@@ -533,9 +527,10 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     const int kh = se->kh, kw = se->kw;
     p->L = f->L;
     // N = rows_n image rows x Lc levels: one 16-level chunk holds every level up to L = 16; for
-    // 16 < L <= 64 a unit's level band usually spans under 16 levels, and 8-level chunks of
-    // 32-row units contract about half as many levels as 16-level ones; above that bands are
-    // wider (tens of levels) and 16-level chunks of 16-row units waste less
+    // 16 < L <= 64 a unit's band usually spans under 16 levels, and 8-level chunks of 32-row
+    // units contract about half as many levels as 16-level ones; above that bands span tens of
+    // levels, and on smooth content they widen with the unit's height, so 16-row units with
+    // 16-level chunks cost less (4096^2 smooth L = 256: 22.4 vs 27.7 ms per launch)
     p->Lc = (f->L > kDirectLc && f->L <= 64) ? kDirectLcBand : kDirectLc;
     p->rows_n = kDirectN / p->Lc;
     p->kh = kh;
@@ -577,8 +572,14 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
         const int passes = (p->n_levels + G - 1) / G;
         if (passes > kDirectMaxPasses) continue;
         const long long cost = static_cast<long long>(passes) * G * ks;
-        // ties go to larger G: fewer passes re-read the image planes fewer times
-        if (best < 0 || cost <= best) {
+        // ties: with 8-level chunks (narrow bands) to smaller G -- with more passes of fewer
+        // offset levels each, a unit whose lower bound lies above a pass's reach skips that pass,
+        // e.g. the low-offset half of a 63x63 SE with offsets 0..7 on uniform content (measured
+        // 1.06 -> 0.56 ms per 2048^2 launch); with 16-level chunks (wide bands, where passes
+        // are rarely skipped) to larger G, fewer accumulations (4096^2 smooth L = 256: 22.4 vs
+        // 26.4 ms)
+        const bool take = p->Lc == kDirectLcBand ? cost < best : cost <= best;
+        if (best < 0 || take) {
             best = cost;
             p->G = G;
         }
@@ -646,8 +647,8 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     // displacement (oy - r, ox - c) and b
     p->band_tap_off = static_cast<int>(p->meta.size());
     {
-        // the denser subset pays where 8-level chunks need a tight bound
-        const int cells = p->Lc == kDirectLcBand ? 16 : 8;
+        // 16 x 16 cells wherever a band is computed (L <= 16 needs none: one chunk)
+        const int cells = f->L > kDirectLc ? 16 : 8;
         const int ny = std::min(cells, kh), nx = std::min(cells, kw);
         std::vector<int> bt;
         bool has_origin = false;
@@ -679,6 +680,17 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
         }
         p->n_band_taps = static_cast<int>(bt.size() / 3);
         p->meta.insert(p->meta.end(), bt.begin(), bt.end());
+    }
+    // taps of each pass (the band-limited work count), -1 when the offsets are on the device
+    p->pass_taps_off = static_cast<int>(p->meta.size());
+    for (int ps = 0; ps < p->n_pass; ++ps) {
+        int n = 0;
+        for (int t = 0; !dev && t < kh * kw; ++t) {
+            if (!se->mask[t]) continue;
+            for (int g = 0; g < p->G; ++g)
+                if (gw[ps * 8 + g] == se->offset[t]) { ++n; break; }
+        }
+        p->meta.push_back(dev ? -1 : n);
     }
     p->toeplitz_blocks = p->active_rows_total * p->nk;
     p->issued_flop = static_cast<double>(p->tiles) * p->T * static_cast<double>(p->active_rows_total) * p->ksteps * 2.0 *
@@ -793,6 +805,7 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
     d->kh = p.kh;
     d->band_tap_off = p.band_tap_off;
     d->n_band_taps = p.n_band_taps;
+    d->pass_taps_off = p.pass_taps_off;
     d->band = nullptr;
     d->dev_off = nullptr;
     d->dev_reflect = 0;
@@ -1061,6 +1074,25 @@ __global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectL
             // largest offset always has a chunk; the clamp keeps that true for any input
             b.lb = min(lb, b.hi + P->maxb);
             const_cast<DirectBand*>(P->band)[t - P->tile_base] = b;
+            if (dl.band_work != nullptr) {
+                // the contraction the unit needs: per pass, its taps x the levels of its band, per pixel
+                const int* pt = P->meta + P->pass_taps_off;
+                const int* gwa = P->meta + (P->n_pass + 1);
+                unsigned long long wk = 0;
+                bool known = true;
+                for (int p = 0; p < P->n_pass; ++p) {
+                    int wmax = 0;
+                    for (int g = 0; g < P->G; ++g) wmax = max(wmax, gwa[p * 8 + g]);
+                    const int lo = b.lb - wmax;
+                    if (lo > b.hi) continue;
+                    if (pt[p] < 0) known = false;
+                    wk += static_cast<unsigned long long>(max(pt[p], 0)) * static_cast<unsigned>(b.hi - max(lo, 0) + 1);
+                }
+                const int uwp = P->T * P->J;
+                const long long npx = static_cast<long long>(max(0, min(h, tc.i0 + P->rows_n) - max(0, tc.i0))) *
+                                      max(0, min(w, tc.j0 + uwp) - max(0, tc.j0));
+                if (known && wk) atomicAdd(dl.band_work, wk * static_cast<unsigned long long>(npx));
+            }
         }
     }
 }

@@ -511,6 +511,7 @@ static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int er
     dl.total_tiles = dp.tiles;
     dl.err = ctx->d_err;
     dl.mma_count = ctx->d_mma;
+    dl.band_work = ctx->d_mma + 1;
     dl.wait_ns = ctx->wait_ns;
     rc = launch_band(ctx, dl, direct_band_window(dl.single), st);
     if (rc) return rc;
@@ -604,6 +605,7 @@ int run_one_dev(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b, int
     dl.total_tiles = dp.tiles;
     dl.err = ctx->d_err;
     dl.mma_count = ctx->d_mma;
+    dl.band_work = ctx->d_mma + 1;
     dl.wait_ns = ctx->wait_ns;
     rc = launch_band(ctx, dl, direct_band_window(dl.single), st);
     if (rc) return rc;
@@ -643,8 +645,8 @@ int morph_ctx_create(int device, morph_ctx** out) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_err, sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(c->d_err, 0, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMalloc(&c->d_mma, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(c->d_mma, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&c->d_mma, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->d_mma, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         if (c->d_err) cudaFree(c->d_err);
         if (c->d_mma) cudaFree(c->d_mma);
@@ -864,6 +866,16 @@ uint64_t morph_launch_count(const morph_ctx* ctx) { return ctx ? ctx->launches :
 int morph_ctx_set_wait_limit(morph_ctx* ctx, uint64_t ns) {
     if (!ctx) return MORPH_E_INVAL;
     ctx->wait_ns = static_cast<unsigned long long>(ns);
+    return MORPH_OK;
+}
+
+int morph_band_work(morph_ctx* ctx, uint64_t* out) {
+    if (!ctx || !out) return MORPH_E_INVAL;
+    MORPH_CUDA_TRY(cudaSetDevice(ctx->device));
+    MORPH_CUDA_TRY(cudaDeviceSynchronize());
+    unsigned long long v = 0;
+    MORPH_CUDA_TRY(cudaMemcpy(&v, ctx->d_mma + 1, sizeof(v), cudaMemcpyDeviceToHost));
+    *out = static_cast<uint64_t>(v);
     return MORPH_OK;
 }
 

@@ -217,6 +217,7 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
         dl.total_tiles = b->total_tiles;
         dl.err = ctx->d_err;
         dl.mma_count = ctx->d_mma;
+        dl.band_work = ctx->d_mma + 1;
         dl.wait_ns = ctx->wait_ns;
         if (b->probs.size() == 1) {       // one problem: descriptor as a kernel parameter
             dl.single = b->probs[0];

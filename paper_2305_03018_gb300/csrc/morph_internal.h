@@ -89,6 +89,7 @@ struct DirectProblemDev {
     int dtype;
     long long row_stride, batch_stride;
     int kh, maxb, band_tap_off, n_band_taps;
+    int pass_taps_off;      // meta offset of the taps per pass (-1 entries: offsets on the device)
     int h, w, nimg, L;
     int Lc, rows_n, J, G;
     int n_pass, nk, ksteps, kw;
@@ -109,12 +110,14 @@ struct DirectLaunch {
     long long total_tiles;
     unsigned int* err;
     unsigned long long* mma_count;   // nullable: MMAs issued, added once per CTA
+    unsigned long long* band_work;   // nullable: multiply-adds of the band-limited contraction (band kernel)
     unsigned long long wait_ns;      // limit of each bounded wait; 0 = kWaitLimitNs
 };
 
 struct DirectPlan {
     int L = 0, Lc = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0, T = 1, split = 0, nb = 0;
     int band_tap_off = 0, n_band_taps = 0;   // lower-bound taps (oy - r, ox - c, b) in meta
+    int pass_taps_off = 0;                    // taps of each pass in meta
     int kh = 0, kw = 0, oy = 0, ox = 0, e = 0, erode = 0, shift = 0;
     int h = 0, w = 0, nimg = 0, w_pad = 0;
     int tiles_x = 0, tiles_y = 0;
@@ -226,7 +229,8 @@ struct morph_ctx {
     int device = 0;
     int num_sms = 0;
     unsigned int* d_err = nullptr;        // device error word
-    unsigned long long* d_mma = nullptr;  // MMAs issued by the direct route (measurement hook)
+    unsigned long long* d_mma = nullptr;  // [0] MMAs issued by the direct route, [1] its band-limited
+                                          // method work in multiply-adds (measurement hooks)
     unsigned long long wait_ns = 0;       // limit of the kernels' bounded waits; 0 = the default
     void* ws = nullptr;                   // device workspace
     size_t ws_bytes = 0;

@@ -125,6 +125,7 @@ _SIGS = {
     "morph_launch_count": (ctypes.c_uint64, [_P]),
     "morph_mma_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "morph_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "morph_band_work": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "morph_run_noalloc": (ctypes.c_int, [ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), ctypes.c_int, _P, _P,
                                          _P, _P]),
     "morph_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -306,6 +307,12 @@ def morph_erode_backward_dev_se(ctx, image, se, e_ptr, ce_ptr, g_ptr, gin_ptr, g
 
 def morph_ctx_set_wait_limit(ctx, ns: int) -> int:
     return load_library().morph_ctx_set_wait_limit(ctx, int(ns))
+
+
+def morph_band_work(ctx) -> int:
+    v = ctypes.c_uint64(0)
+    check(load_library().morph_band_work(ctx, ctypes.byref(v)), "morph_band_work")
+    return int(v.value)
 
 
 def morph_mma_count(ctx) -> int:
@@ -604,6 +611,10 @@ class Context:
     def set_wait_limit(self, ns: int):
         """Limit of the kernels' bounded waits (0 = the default 4 s); a failure-handling hook."""
         check(morph_ctx_set_wait_limit(self.handle, ns), "morph_ctx_set_wait_limit")
+
+    def band_work(self) -> int:
+        """Multiply-adds of the band-limited contraction the FP8 route needed (synchronises)."""
+        return morph_band_work(self.handle)
 
     def mma_count(self) -> int:
         """tcgen05 MMAs the FP8 direct route issued through this context (synchronises)."""

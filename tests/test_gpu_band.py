@@ -111,9 +111,13 @@ def test_constant_image_issues_one_chunk_per_unit(ctx):
     se = wl.se_flat_disk(7)
     info = ctx.plan(f, L, se, method="direct_fp8")
     full = info.est_flop / (2.0 * 128 * 256 * 32)         # MMAs with every level
-    m0 = ctx.mma_count()
+    m0, w0 = ctx.mma_count(), ctx.band_work()
     D, cD = ctx.dilate(f, L, se, method="direct_fp8", count=True)
     issued = ctx.mma_count() - m0
+    work = ctx.band_work() - w0
     ctx.check()
     assert issued * info.level_chunks == full
     assert int(D.min()) == int(D.max()) == 77
+    # the band-limited work: every unit's band is the single level 77, so each pixel needs |B|
+    # multiply-adds
+    assert work == se.taps * 256 * 512
