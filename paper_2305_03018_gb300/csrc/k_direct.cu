@@ -21,8 +21,9 @@
 //             row x grey level, K = a window of image columns;
 //   D       : 128 x 256 FP32 accumulator in TMEM.
 // M = 128 stacks G offset groups x J = 128 / G output columns, N = 256
-// stacks rows_n image rows x Lc grey levels (16 x 16 when L <= 16, else
-// 32 x 8).  A unit's levels are covered in chunks of Lc from the top of its
+// stacks rows_n image rows x Lc grey levels (16 x 16 when L <= 16 or L > 64,
+// 64 x 4 -- or 32 x 8 with offsets beyond 4095 - L -- when 16 < L <= 64).
+// A unit's levels are covered in chunks of Lc from the top of its
 // level band (see "level bands" below): Step 3 needs only the degrees at or
 // above each pixel's dilation value.  The epilogue reads a lane per (group,
 // column), finds each group's top level by a descending scan and combines
@@ -60,9 +61,11 @@ constexpr int kStages = 3;
 constexpr int kStageA = 128 * 128;             // 16 KB: 128 Toeplitz rows x 128 B of K
 constexpr int kStageB = kDirectN * 128;        // 32 KB: 256 (row, level) rows x 128 B of K
 constexpr int kStageBytes = kStageA + kStageB;
-constexpr int kRedEntries = 2 * 32 * 128;      // two tiles x rows_n (<= 32) x 128 lanes, 4 B each: both tiles
-                                               // of a two-tile unit are read out before either is reduced
-constexpr int kRunEntries = 4096;              // rows_n x J x T (<= 4096: 32 x 128, or 16 x 128 x 2)
+constexpr int kRedEntries = 2 * 32 * 128;      // rows_n x 128 lanes, 4 B each; with rows_n <= 32 both tiles of
+                                               // a two-tile unit are read out before either is reduced
+constexpr int kRunEntries = 4096;              // rows_n x J x T (int2: <= 32 x 128, or 16 x 128 x 2)
+constexpr int kRunPacked = 2 * kRunEntries;    // the same 32 KB as packed uint32 entries (4-level plans: 64 x 128)
+constexpr int kDirectNarrowMinMmas = 96;       // MMAs per accumulation below which 4-level plans do not pay
 constexpr int kDirectThreads = 192;
 constexpr uint32_t kTmemCols = 2 * kDirectN;   // two accumulators
 
@@ -106,13 +109,34 @@ __device__ __forceinline__ TileCoord direct_tile(const DirectProblemDev* P, long
     return c;
 }
 
-// The unit's level band (see DirectBand); without a band buffer every level
-// is covered.
+// Image rows of a unit that the band kernel takes at a time: a 64-row unit
+// has two band entries, which the direct kernel combines.
+constexpr int kBandSlabRows = 32;
+
+__host__ __device__ __forceinline__ int band_slabs(int rows_n) { return (rows_n + kBandSlabRows - 1) / kBandSlabRows; }
+
+// The unit's level band (see DirectBand), from its slabs' entries: hi = the
+// largest level in their windows (-1: none read), lb = the smallest of their
+// lower bounds (INT_MAX: no pixel).  Without a band buffer every level is
+// covered.
 __device__ __forceinline__ DirectBand direct_band(const DirectProblemDev* P, long long t) {
-    if (P->band != nullptr) return P->band[t - P->tile_base];
     DirectBand b;
-    b.hi = P->L - 1;
-    b.lb = -1;
+    if (P->band == nullptr) {
+        b.hi = P->L - 1;
+        b.lb = -1;
+        return b;
+    }
+    const int ns = band_slabs(P->rows_n);
+    const DirectBand* e = P->band + (t - P->tile_base) * ns;
+    b = e[0];
+    for (int k = 1; k < ns; ++k) {
+        b.hi = max(b.hi, e[k].hi);
+        b.lb = min(b.lb, e[k].lb);
+    }
+    b.hi = b.hi < 0 ? P->L - 1 : b.hi;          // no pixel read: the unit's pixels have no valid tap
+    // lb <= D(x) <= hi + max b for every pixel with a valid tap, so the pass holding the largest
+    // offset always has a chunk; the clamp keeps that true for any input
+    b.lb = min(b.lb, b.hi + P->maxb);
     return b;
 }
 
@@ -140,6 +164,32 @@ __device__ __forceinline__ bool epi_any_failed(bool failed) {
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+// One lane's read-out of an accumulator: N = 256 / LC image rows x LC levels, 32 columns
+// (32 / LC rows) per TMEM load.  Each row's result is (top level in the chunk + 1) << 20 | its
+// count (0: no level set; counts <= |B| <= 512^2 < 2^20), stored at red_m[row * 128].
+template <int LC>
+__device__ __forceinline__ void epi_read_rows(uint32_t trow, uint32_t* red_m) {
+    constexpr int kRowsPerLoad = 32 / LC;
+    for (int tr0 = 0; tr0 < kDirectN / LC; tr0 += kRowsPerLoad) {
+        float v[32];
+        tmem_ld_32x32b_x32(trow + static_cast<uint32_t>(tr0 * LC), v);
+        tc_wait_ld();
+#pragma unroll
+        for (int a = 0; a < kRowsPerLoad; ++a) {
+            int top = -1;
+            float cnt = 0.f;
+#pragma unroll
+            for (int k = 0; k < LC; ++k)
+                if (v[a * LC + k] > 0.5f) {
+                    top = k;
+                    cnt = v[a * LC + k];
+                }
+            red_m[(tr0 + a) * 128] =
+                top >= 0 ? (static_cast<uint32_t>(top + 1) << 20) | static_cast<uint32_t>(__float2int_rn(cnt)) : 0u;
+        }
+    }
+}
+
 // TT = 1, 2 or 3: every problem of the launch has that unit kind (one tile,
 // two tiles in one K block, two split tiles; the compiler specialises the MMA
 // issue loop); TT = 0: read the kind per problem.
@@ -147,10 +197,12 @@ template <int TT>
 __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_constant__ DirectLaunch dl) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    // red: one lane's result of one image row of one chunk, (top level in the chunk + 1) << 20 |
-    // its count (0: no level set; counts <= |B| <= 512^2 < 2^20); run: (degree, count) so far
+    // red: one lane's result of one image row of one chunk (epi_read_rows); run: (degree, count)
+    // so far per output pixel, as int2, or packed (degree + 1) << 20 | count in 4-level plans,
+    // whose degrees stay below L + max b <= kDirectNarrowMaxR
     uint32_t* red = reinterpret_cast<uint32_t*>(base + kStages * kStageBytes);
     int2* run = reinterpret_cast<int2*>(red + kRedEntries);
+    uint32_t* runp = reinterpret_cast<uint32_t*>(run);
     DirectSmemTail* tail = reinterpret_cast<DirectSmemTail*>(run + kRunEntries);
     volatile int* abort_flag = &tail->abort;
     const unsigned long long wait_ns = dl.wait_ns != 0ull ? dl.wait_ns : kWaitLimitNs;
@@ -252,7 +304,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
             const bool split = (TT == 0) ? (P->split != 0) : (TT == 3);
             const uint64_t boff1 = static_cast<uint64_t>(P->J) >> 4;   // second tile: J bytes further along K
             const int sh1 = P->J >> 5;                                  // the same shift in 32-byte K steps
-            const int ksteps = P->ksteps, nk = P->nk, nb = P->nb;
+            const int ksteps = P->ksteps, nb = P->nb;
             const DirectBand bd = direct_band(P, t);
             for (int p = 0; ok && p < P->n_pass; ++p) {
               const int nch = direct_pass_chunks(P, bd, p);
@@ -348,6 +400,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         const int et = threadIdx.x - 64;              // 0..127
         uint32_t use0 = 0u, use1 = 0u;   // same slot-claim sequence as the MMA issuer
         uint32_t next_slot = 0;
+        unsigned long long band_wk = 0;  // band-limited multiply-adds of this CTA's units (measurement hook)
         for (long long t = blockIdx.x; t < dl.total_tiles; t += gridDim.x) {
             const DirectProblemDev* P = direct_find(dl, t);
             const TileCoord tc = direct_tile(P, t);
@@ -356,6 +409,24 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
             const DirectBand bd = direct_band(P, t);
             int n_units = 0;                              // accumulations of this unit, all passes
             for (int p = 0; p < P->n_pass; ++p) n_units += direct_pass_chunks(P, bd, p);
+            if (et == 0 && dl.band_work != nullptr && P->band != nullptr) {
+                // the contraction the unit needs: per pass, its taps x the levels of its band, per
+                // pixel (taps unknown, -1, when the offsets are on the device: not counted)
+                const int* pt = P->meta + P->pass_taps_off;
+                unsigned long long wk = 0;
+                bool known = true;
+                for (int p = 0; p < P->n_pass; ++p) {
+                    int wmax = 0;
+                    for (int g = 0; g < G; ++g) wmax = max(wmax, gw[p * 8 + g]);
+                    const int lo = bd.lb - wmax;
+                    if (lo > bd.hi) continue;
+                    if (pt[p] < 0) known = false;
+                    wk += static_cast<unsigned long long>(max(pt[p], 0)) * static_cast<unsigned>(bd.hi - max(lo, 0) + 1);
+                }
+                const long long npx = static_cast<long long>(max(0, min(P->h, tc.i0 + rows_n) - max(0, tc.i0))) *
+                                      max(0, min(P->w, tc.j0 + T * J) - max(0, tc.j0));
+                if (known) band_wk += wk * static_cast<unsigned long long>(npx);
+            }
             bool failed = false;
             int p = 0, ch = 0, nch = direct_pass_chunks(P, bd, 0);
             for (int u = 0; u < n_units; ++u, ++ch) {
@@ -377,6 +448,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 // group gg's degree of the chunk's level k is lev0 + k + its offset
                 const int pairs = rows_n * J;
                 const int* gwp = gw + p * 8;
+                const bool packed = Lc == kDirectLcNarrow;
                 auto reduce = [&](int tt, int rbase) {
                     for (int idx = et; idx < pairs; idx += 128) {
                         const int tr = idx / J, jl = idx - tr * J;
@@ -392,12 +464,23 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                         int2 cur = make_int2(best, bc);
                         const int ri = tt * pairs + idx;
                         if (u > 0) {
-                            const int2 prev = run[ri];
+                            int2 prev;
+                            if (packed) {
+                                const uint32_t e = runp[ri];
+                                prev = make_int2(static_cast<int>(e >> 20) - 1, static_cast<int>(e & 0xFFFFFu));
+                            } else {
+                                prev = run[ri];
+                            }
                             if (prev.x > cur.x) cur = prev;
                             else if (prev.x == cur.x && cur.x >= 0) cur.y += prev.y;
                         }
-                        run[ri] = cur;
-                        if (u == n_units - 1) {
+                        if (u < n_units - 1) {
+                            if (packed)
+                                runp[ri] = cur.x < 0 ? 0u
+                                                     : (static_cast<uint32_t>(cur.x + 1) << 20) | static_cast<uint32_t>(cur.y);
+                            else
+                                run[ri] = cur;
+                        } else {
                             const int i = tc.i0 + tr, j = tc.j0 + tt * J + jl;
                             if (i < P->h && j >= 0 && j < P->w) {
                                 const int dval = cur.x < 0 ? 0 : cur.x;
@@ -416,29 +499,9 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                     const int rbase = reads_first ? tt * rows_n * 128 : 0;
                     const uint32_t trow =
                         tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + (s0 + tt) * kDirectN;
-                    for (int tr = 0; tr < rows_n; ++tr) {
-                        const uint32_t col0 = static_cast<uint32_t>(tr * Lc);
-                        int top = -1;
-                        float cnt = 0.f;
-                        if (Lc == 8) {
-                            float v[8];
-                            tmem_ld_32x32b_x8(trow + col0, v);
-                            tc_wait_ld();
-#pragma unroll
-                            for (int k = 0; k < 8; ++k)
-                                if (v[k] > 0.5f) { top = k; cnt = v[k]; }
-                        } else {                                  // Lc == 16
-                            float v[16];
-                            tmem_ld_32x32b_x16(trow + col0, v);
-                            tc_wait_ld();
-#pragma unroll
-                            for (int k = 0; k < 16; ++k)
-                                if (v[k] > 0.5f) { top = k; cnt = v[k]; }
-                        }
-                        red[rbase + tr * 128 + m] =
-                            (top >= 0) ? (static_cast<uint32_t>(top + 1) << 20) | static_cast<uint32_t>(__float2int_rn(cnt))
-                                       : 0u;
-                    }
+                    if (Lc == kDirectLcNarrow) epi_read_rows<kDirectLcNarrow>(trow, red + rbase + m);
+                    else if (Lc == kDirectLcBand) epi_read_rows<kDirectLcBand>(trow, red + rbase + m);
+                    else epi_read_rows<kDirectLc>(trow, red + rbase + m);
                     // this accumulator's TMEM reads are done: hand it back
                     tc_fence_before();
                     __syncwarp();
@@ -460,6 +523,7 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
             }
             if (failed) break;
         }
+        if (band_wk != 0ull) atomicAdd(dl.band_work, band_wk);
     }
 
     tc_fence_before();
@@ -526,13 +590,6 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     const bool dev = dev_bound >= 0;
     const int kh = se->kh, kw = se->kw;
     p->L = f->L;
-    // N = rows_n image rows x Lc levels: one 16-level chunk holds every level up to L = 16; for
-    // 16 < L <= 64 a unit's band usually spans under 16 levels, and 8-level chunks of 32-row
-    // units contract about half as many levels as 16-level ones; above that bands span tens of
-    // levels, and on smooth content they widen with the unit's height, so 16-row units with
-    // 16-level chunks cost less (4096^2 smooth L = 256: 22.4 vs 27.7 ms per launch)
-    p->Lc = (f->L > kDirectLc && f->L <= 64) ? kDirectLcBand : kDirectLc;
-    p->rows_n = kDirectN / p->Lc;
     p->kh = kh;
     p->kw = kw;
     p->oy = se->oy;
@@ -563,6 +620,19 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     p->taps = taps;
     p->maxb = maxb;
     p->n_levels = static_cast<int>(levels.size());
+    // N = rows_n image rows x Lc levels: one 16-level chunk holds every level up to L = 16.  For
+    // 16 < L <= 64 a unit's band usually spans a few levels (uniform 2048^2 L = 64 content: at
+    // most 4 in 95 % of 64-row units), so 4-level chunks of 64-row units contract about half the
+    // levels of 8-level chunks of 32-row ones; their running results are packed into 32 bits,
+    // which holds degrees below 4095 (L + max b beyond that takes the 8-level form).  Above
+    // L = 64 bands span tens of levels, and on smooth content they widen with the unit's height,
+    // so 16-row units with 16-level chunks cost less (4096^2 smooth L = 256: 22.4 vs 27.7 ms per
+    // launch with 8-level chunks of 32-row units)
+    if (f->L > kDirectLc && f->L <= 64)
+        p->Lc = f->L + maxb <= kDirectNarrowMaxR ? kDirectLcNarrow : kDirectLcBand;
+    else
+        p->Lc = kDirectLc;
+    p->rows_n = kDirectN / p->Lc;
     if (taps == 0) return MORPH_OK;
     // groups per pass: minimise passes x G x K-steps (the MMA work per output pixel)
     long long best = -1;
@@ -572,13 +642,13 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
         const int passes = (p->n_levels + G - 1) / G;
         if (passes > kDirectMaxPasses) continue;
         const long long cost = static_cast<long long>(passes) * G * ks;
-        // ties: with 8-level chunks (narrow bands) to smaller G -- with more passes of fewer
+        // ties: with 4- or 8-level chunks (narrow bands) to smaller G -- with more passes of fewer
         // offset levels each, a unit whose lower bound lies above a pass's reach skips that pass,
         // e.g. the low-offset half of a 63x63 SE with offsets 0..7 on uniform content (measured
         // 1.06 -> 0.56 ms per 2048^2 launch); with 16-level chunks (wide bands, where passes
         // are rarely skipped) to larger G, fewer accumulations (4096^2 smooth L = 256: 22.4 vs
         // 26.4 ms)
-        const bool take = p->Lc == kDirectLcBand ? cost < best : cost <= best;
+        const bool take = p->Lc < kDirectLc ? cost < best : cost <= best;
         if (best < 0 || take) {
             best = cost;
             p->G = G;
@@ -592,6 +662,22 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     // two tiles per unit when both windows fit one 128-byte stage and the image is wide enough
     // (the second tile's K-steps read up to J + 32 ksteps bytes into the 128-byte rows)
     p->T = (2 * p->J + kw - 1 <= 128 && p->J + 32 * p->ksteps <= 128 && f->w > p->J) ? 2 : 1;
+    if (p->Lc == kDirectLcNarrow) {
+        // 64-row units halve the MMAs of a narrow band but double the epilogue's pixels per
+        // accumulation and halve the units: keep them where an accumulation's MMAs outlast its
+        // epilogue and the launch has two waves of units (64 x 1 x 128 x 128, 9 x 9 SE: 0.109 ms
+        // with 32-row units, 0.135 ms with 64-row ones)
+        int se_rows = 0;
+        for (int r = 0; r < kh; ++r)
+            for (int c = 0; c < kw; ++c)
+                if (se->mask[r * kw + c]) {
+                    ++se_rows;
+                    break;
+                }
+        const long long units = static_cast<long long>(f->n) * ((f->h + 63) / 64) * ((f->w + p->T * p->J - 1) / (p->T * p->J));
+        if (se_rows * p->ksteps * p->T < kDirectNarrowMinMmas || units < kDirectSplitMinUnits) p->Lc = kDirectLcBand;
+        p->rows_n = kDirectN / p->Lc;
+    }
     p->split = 0;
     p->nb = p->nk;
     // K windows start at image column j0 - (kw - 1 - ox): shifting the planes by that amount mod 32
@@ -600,7 +686,8 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     p->shift = (((kw - 1 - se->ox) % 32) + 32) % 32;
     p->e = 0;
     p->tiles_y = (f->h + p->rows_n - 1) / p->rows_n;
-    if (p->T == 1 && p->J >= 32 && f->w > p->J && 2 * p->rows_n * p->J <= kRunEntries) {
+    const int run_cap = p->Lc == kDirectLcNarrow ? kRunPacked : kRunEntries;
+    if (p->T == 1 && p->J >= 32 && f->w > p->J && 2 * p->rows_n * p->J <= run_cap) {
         // split two-tile units: fewer staged blocks per SE row for both tiles; J a multiple of 32
         // keeps each K step inside one 128-byte row, both tiles' running pairs fit the run buffer
         const int nb = (p->J + 32 * p->ksteps + 127) / 128;
@@ -842,8 +929,10 @@ void direct_fill_band(DirectProblemDev* d, const morph_image* f, DirectBand* ban
 }
 
 size_t direct_band_bytes(const morph_image* f) {
-    // units are rows_n >= 16 image rows by at least 16 columns
-    const size_t units = static_cast<size_t>(f->n) * ((f->h + 15) / 16) * ((f->w + 15) / 16);
+    // units are rows_n >= 16 image rows by at least 16 columns, with one entry per 32-row slab:
+    // at most one entry per 16 image rows, or two for a 64-row unit over an image of <= 16 rows
+    const size_t rows = std::max<size_t>((f->h + 15) / 16, 2);
+    const size_t units = static_cast<size_t>(f->n) * rows * ((f->w + 15) / 16);
     return (units * sizeof(DirectBand) + 255) & ~size_t(255);
 }
 
@@ -887,17 +976,34 @@ __device__ __forceinline__ int band_level(const DirectProblemDev* P, long long i
     return P->erode ? P->L - 1 - v : v;
 }
 
+// Pixel pairs and the staged window.  A thread takes pixel pairs (j, j + s) of a slab row,
+// s = min(32, uw / 2): the first pixels of a row are the first s of each 2 s columns.  The
+// window is staged as q[r][k] = (level(r, k), level(r, k + s)), k < WQ, so a pair reads a tap's
+// two sources with one 4-byte load, and the lanes of a warp, which take consecutive first
+// pixels, load consecutive words.  The row pitch WQ is s mod 32 when s < 32, so the rows one
+// warp covers start on distinct banks.
+__host__ __device__ __forceinline__ int band_pair_stride(int uw) { return uw >= 64 ? 32 : (uw >> 1); }
+__host__ __device__ __forceinline__ int band_pitch(int uw, int kw) {
+    const int s = band_pair_stride(uw);
+    int wq = uw - s + kw - 1;                  // first pixels j <= uw - s - 1 read columns <= j + kw - 1
+    if (s < 32) wq += ((s - wq) % 32 + 32) % 32;
+    return wq;
+}
+
 // Warp `warp` stages window rows rr = warp, warp + nwarp, ...: its (row, 32-column
-// group) items are taken eight at a time, so each lane has eight loads in flight
+// group) items are taken a batch at a time, so each lane has several loads in flight
 // before it stores their levels (the staging is bound by load latency otherwise).
+// Columns WQ + s are staged (the highs of the last pairs); levels of the unit's true
+// window, W = uw + kw - 1 columns, give the returned maximum.
 constexpr int kBandStageBatch = 6;         // staging loads in flight per lane
 
 template <typename Pix>
 __device__ __forceinline__ int band_stage_rows(const DirectProblemDev* P, long long ibase, int wr0, int wc0, int WR,
-                                               int WC, __half* qh, int warp, int nwarp, int lane) {
+                                               int WQ, int ps, int W, __half* qh, int warp, int nwarp, int lane) {
     const Pix* src = static_cast<const Pix*>(P->src);
     const int h = P->h, w = P->w, L = P->L, flip = P->erode;
-    const int ng = (WC + 31) >> 5;                                 // 32-column groups per row
+    const int WS = WQ + ps;                                        // staged columns per row
+    const int ng = (WS + 31) >> 5;                                 // 32-column groups per row
     const int my_rows = warp < WR ? (WR - warp + nwarp - 1) / nwarp : 0;
     const int items = my_rows * ng;
     int hi = -1;
@@ -909,9 +1015,9 @@ __device__ __forceinline__ int band_stage_rows(const DirectProblemDev* P, long l
         for (int k = 0; k < kBandStageBatch; ++k) {
             const int rr = warp + r * nwarp;
             cc[k] = gcol * 32 + lane;
-            e[k] = rr * WC + cc[k];
+            e[k] = rr * WQ;
             const int i = wr0 + rr, j = wc0 + cc[k];
-            in[k] = base + k < items && cc[k] < WC && i >= 0 && i < h && j >= 0 && j < w;
+            in[k] = base + k < items && cc[k] < WS && i >= 0 && i < h && j >= 0 && j < w;
             v[k] = in[k] ? static_cast<int>(src[ibase + static_cast<long long>(i) * P->row_stride + j]) : 0;
             if (++gcol == ng) {
                 gcol = 0;
@@ -920,31 +1026,37 @@ __device__ __forceinline__ int band_stage_rows(const DirectProblemDev* P, long l
         }
 #pragma unroll
         for (int k = 0; k < kBandStageBatch; ++k) {
-            if (base + k >= items || cc[k] >= WC) continue;
+            if (base + k >= items || cc[k] >= WS) continue;
             float fv = -4096.f;
             if (in[k]) {
                 int lv = min(max(v[k], 0), L - 1);    // out-of-range values are reported by the encoder
                 lv = flip ? L - 1 - lv : lv;
-                hi = max(hi, lv);
+                if (cc[k] < W) hi = max(hi, lv);
                 fv = static_cast<float>(lv);
             }
             const __half hv = __float2half_rn(fv);
-            qh[2 * e[k]] = hv;                                     // low half of pair cc
-            if (cc[k] > 0) qh[2 * e[k] - 1] = hv;                  // high half of pair cc - 1
-            if (cc[k] == WC - 1) qh[2 * e[k] + 1] = __float2half_rn(-4096.f);   // the row's last pair
+            if (cc[k] < WQ) qh[2 * (e[k] + cc[k])] = hv;                   // low half of entry cc
+            if (cc[k] >= ps) qh[2 * (e[k] + cc[k] - ps) + 1] = hv;         // high half of entry cc - s
         }
     }
     return hi;
 }
 
+union BandH2 {
+    __half2 h;
+    unsigned int u;
+};
+
 // The thread's minimum over its NP pixel pairs of the subset maximum: pair k of
-// thread t is pair t + 256 k of the unit, row-major (uw / 2 pairs per row).
+// thread t is pair t + 256 k of the slab, row-major (uw / 2 pairs per row).
 // Two accumulators per pair take alternate taps, so consecutive taps do not
-// wait on each other.
+// wait on each other; a tap pair's offsets and offsets' weights are read with
+// one 8-byte load each.
 template <int NP>
 __device__ __forceinline__ int band_lower(const DirectProblemDev* P, const TileCoord& tc, const __half2* q,
-                                          const int* s_toff, const __half2* s_tw, int ntap, int WC, int npair) {
+                                          const int* s_toff, const __half2* s_tw, int ntap, int WQ, int npair) {
     const int uw = P->T * P->J, half_w = uw >> 1, sh = __ffs(half_w) - 1;
+    const int ps = band_pair_stride(uw), psh = __ffs(ps) - 1;
     if (static_cast<int>(threadIdx.x) >= npair) return 0x7fffffff;   // (NP == 1 with fewer pairs than threads)
     __half2 a0[NP], a1[NP];
     int base[NP];
@@ -953,17 +1065,23 @@ __device__ __forceinline__ int band_lower(const DirectProblemDev* P, const TileC
         a0[k] = __floats2half2_rn(-1.f, -1.f);
         a1[k] = a0[k];
         const int pp = threadIdx.x + k * 256;
-        const int pr = pp >> sh, pc = 2 * (pp & (half_w - 1));
-        base[k] = (pr + P->kh - 1 - P->oy) * WC + pc + P->kw - 1 - P->ox;
+        const int pr = pp >> sh, c = pp & (half_w - 1);
+        const int j = ((c >> psh) << (psh + 1)) + (c & (ps - 1));
+        base[k] = (pr + P->kh - 1 - P->oy) * WQ + j + P->kw - 1 - P->ox;
     }
+    const int2* toff2 = reinterpret_cast<const int2*>(s_toff);
+    const uint2* tw2 = reinterpret_cast<const uint2*>(s_tw);
     int s = 0;
     for (; s + 1 < ntap; s += 2) {
-        const int o0 = s_toff[s], o1 = s_toff[s + 1];
-        const __half2 w0 = s_tw[s], w1 = s_tw[s + 1];
+        const int2 o = toff2[s >> 1];
+        const uint2 wu = tw2[s >> 1];
+        BandH2 w0, w1;
+        w0.u = wu.x;
+        w1.u = wu.y;
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-            a0[k] = __hmax2(a0[k], __hadd2(q[base[k] + o0], w0));
-            a1[k] = __hmax2(a1[k], __hadd2(q[base[k] + o1], w1));
+            a0[k] = __hmax2(a0[k], __hadd2(q[base[k] + o.x], w0.h));
+            a1[k] = __hmax2(a1[k], __hadd2(q[base[k] + o.y], w1.h));
         }
     }
     if (s < ntap) {
@@ -976,69 +1094,78 @@ __device__ __forceinline__ int band_lower(const DirectProblemDev* P, const TileC
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const int pp = threadIdx.x + k * 256;
-        const int i = tc.i0 + (pp >> sh), j = tc.j0 + 2 * (pp & (half_w - 1));
+        const int c = pp & (half_w - 1);
+        const int i = tc.i0 + (pp >> sh), j = tc.j0 + ((c >> psh) << (psh + 1)) + (c & (ps - 1));
         if (i >= P->h) continue;
         const float2 m = __half22float2(__hmax2(a0[k], a1[k]));
         if (j >= 0 && j < P->w) lb = min(lb, static_cast<int>(m.x));
-        if (j + 1 >= 0 && j + 1 < P->w) lb = min(lb, static_cast<int>(m.y));
+        if (j + ps >= 0 && j + ps < P->w) lb = min(lb, static_cast<int>(m.y));
     }
     return lb;
 }
 
-__global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectLaunch dl, int win_bytes) {
-    // The unit's input window (rows i - r + oy, columns j - c + ox over the SE box, not
-    // clipped) as overlapping half2 pairs q[r][k] = (level(r, k), level(r, k + 1)), -4096
-    // outside the image; a pixel pair (j, j + 1) reads a tap's two sources with one load.
-    // Sums level + min(b, 1024) <= 1279 and the sentinel -4096 + 1024 are exact in fp16.
+__global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectLaunch dl, int win_bytes, int slabs) {
+    // One work item per unit slab (kBandSlabRows image rows of a unit; item s T + t is slab s of
+    // unit t, T units in the launch, and units with fewer slabs skip the items past theirs).
+    // The slab's input window (rows i - r + oy, columns j - c + ox over the SE box, not clipped)
+    // is staged as half2 pairs q[r][k] = (level(r, k), level(r, k + s)) (band_pitch), -4096
+    // outside the image.  Sums level + min(b, 1024) <= 1279 and the sentinel -4096 + 1024 are
+    // exact in fp16.
     extern __shared__ __align__(16) uint8_t s_raw[];
     __half* qh = reinterpret_cast<__half*>(s_raw);
     const __half2* q = reinterpret_cast<const __half2*>(s_raw);
     __shared__ int s_hi[8], s_lb[8];
-    __shared__ int s_toff[kBandTapsMax];
-    __shared__ __half2 s_tw[kBandTapsMax];
+    __shared__ __align__(8) int s_toff[kBandTapsMax];
+    __shared__ __align__(8) __half2 s_tw[kBandTapsMax];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    for (long long t = blockIdx.x; t < dl.total_tiles; t += gridDim.x) {
+    for (long long it = blockIdx.x; it < slabs * dl.total_tiles; it += gridDim.x) {
+        const int sl = static_cast<int>(it / dl.total_tiles);
+        const long long t = it - sl * dl.total_tiles;
         const DirectProblemDev* P = direct_find(dl, t);
-        if (P->band == nullptr) continue;             // every level (block-uniform branch)
-        const TileCoord tc = direct_tile(P, t);
+        if (P->band == nullptr || sl >= band_slabs(P->rows_n)) continue;   // block-uniform
+        TileCoord tc = direct_tile(P, t);
+        tc.i0 += sl * kBandSlabRows;
         const int h = P->h, w = P->w, uw = P->T * P->J, ntap = min(P->n_band_taps, kBandTapsMax);
+        const int rows = min(P->rows_n, kBandSlabRows);
         const long long ibase = static_cast<long long>(tc.n) * P->batch_stride;
         const int wr0 = tc.i0 - (P->kh - 1 - P->oy), wc0 = tc.j0 - (P->kw - 1 - P->ox);
-        const int WR = P->rows_n + P->kh - 1, WC = uw + P->kw;   // one spare column for the pairs
-        const bool fast = static_cast<long long>(WR) * WC * 4 <= win_bytes &&
-                          P->rows_n * (uw >> 1) <= 256 * kBandPairs;      // block-uniform
-        __syncthreads();   // the previous unit's readers of the shared arrays are done
+        const int WR = rows + P->kh - 1, WQ = band_pitch(uw, P->kw);
+        const bool fast = static_cast<long long>(WR) * WQ * 4 <= win_bytes &&
+                          rows * (uw >> 1) <= 256 * kBandPairs;      // block-uniform
+        __syncthreads();   // the previous item's readers of the shared arrays are done
         for (int k = threadIdx.x; k < ntap; k += blockDim.x) {
             const int* tp = P->meta + P->band_tap_off + 3 * k;
-            s_toff[k] = tp[0] * WC + tp[1];
+            s_toff[k] = tp[0] * WQ + tp[1];
             const float wv = static_cast<float>(min(band_tap_offset(P, tp[2]), kBandWMax));
             s_tw[k] = __floats2half2_rn(wv, wv);
         }
         int hi = -1;
         int lb = 0x7fffffff;
-        if (fast) {
+        if (tc.i0 >= h) {
+            // a slab below the image: no pixel, no window (hi -1, lb INT_MAX)
+        } else if (fast) {
+            const int ps = band_pair_stride(uw), W = uw + P->kw - 1;
             if (P->dtype == MORPH_U8)
-                hi = band_stage_rows<uint8_t>(P, ibase, wr0, wc0, WR, WC, qh, warp, nwarp, lane);
+                hi = band_stage_rows<uint8_t>(P, ibase, wr0, wc0, WR, WQ, ps, W, qh, warp, nwarp, lane);
             else if (P->dtype == MORPH_U16)
-                hi = band_stage_rows<uint16_t>(P, ibase, wr0, wc0, WR, WC, qh, warp, nwarp, lane);
+                hi = band_stage_rows<uint16_t>(P, ibase, wr0, wc0, WR, WQ, ps, W, qh, warp, nwarp, lane);
             else
-                hi = band_stage_rows<int32_t>(P, ibase, wr0, wc0, WR, WC, qh, warp, nwarp, lane);
+                hi = band_stage_rows<int32_t>(P, ibase, wr0, wc0, WR, WQ, ps, W, qh, warp, nwarp, lane);
             __syncthreads();
-            // pixel pairs of the unit: rows_n rows x uw / 2 pairs per row, npair / 256 per thread
+            // pixel pairs of the slab: rows x uw / 2 pairs per row, npair / 256 per thread
             // (a power of two; with fewer pairs than threads, one pair for the first npair threads)
-            const int npair = P->rows_n * (uw >> 1);
-            if (npair <= 256) lb = band_lower<1>(P, tc, q, s_toff, s_tw, ntap, WC, npair);
-            else if (npair <= 512) lb = band_lower<2>(P, tc, q, s_toff, s_tw, ntap, WC, npair);
-            else if (npair <= 1024) lb = band_lower<4>(P, tc, q, s_toff, s_tw, ntap, WC, npair);
-            else lb = band_lower<8>(P, tc, q, s_toff, s_tw, ntap, WC, npair);
+            const int npair = rows * (uw >> 1);
+            if (npair <= 256) lb = band_lower<1>(P, tc, q, s_toff, s_tw, ntap, WQ, npair);
+            else if (npair <= 512) lb = band_lower<2>(P, tc, q, s_toff, s_tw, ntap, WQ, npair);
+            else if (npair <= 1024) lb = band_lower<4>(P, tc, q, s_toff, s_tw, ntap, WQ, npair);
+            else lb = band_lower<8>(P, tc, q, s_toff, s_tw, ntap, WQ, npair);
         } else {
             // windows too large for shared memory (SE boxes of hundreds of rows): direct loads
-            const int r0 = max(0, wr0), r1 = min(h, tc.i0 + P->rows_n + P->oy);
+            const int r0 = max(0, wr0), r1 = min(h, tc.i0 + rows + P->oy);
             const int c0 = max(0, wc0), c1 = min(w, tc.j0 + uw + P->ox);
             for (int i = r0 + warp; i < r1; i += nwarp)
                 for (int j = c0 + lane; j < c1; j += 32) hi = max(hi, band_level(P, ibase, i, j));
-            __syncthreads();
-            const int pi0 = max(0, tc.i0), pi1 = min(h, tc.i0 + P->rows_n);
+            const int pi0 = max(0, tc.i0), pi1 = min(h, tc.i0 + rows);
             const int pj0 = max(0, tc.j0), pj1 = min(w, tc.j0 + uw);
             for (int i = pi0 + warp; i < pi1; i += nwarp)
                 for (int j = pj0 + lane; j < pj1; j += 32) {
@@ -1069,48 +1196,30 @@ __global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectL
                 lb = min(lb, s_lb[k]);
             }
             DirectBand b;
-            b.hi = hi < 0 ? P->L - 1 : hi;            // no pixel read: the unit's pixels have no valid tap
-            // lb <= D(x) <= hi + max b for every pixel with a valid tap, so the pass holding the
-            // largest offset always has a chunk; the clamp keeps that true for any input
-            b.lb = min(lb, b.hi + P->maxb);
-            const_cast<DirectBand*>(P->band)[t - P->tile_base] = b;
-            if (dl.band_work != nullptr) {
-                // the contraction the unit needs: per pass, its taps x the levels of its band, per pixel
-                const int* pt = P->meta + P->pass_taps_off;
-                const int* gwa = P->meta + (P->n_pass + 1);
-                unsigned long long wk = 0;
-                bool known = true;
-                for (int p = 0; p < P->n_pass; ++p) {
-                    int wmax = 0;
-                    for (int g = 0; g < P->G; ++g) wmax = max(wmax, gwa[p * 8 + g]);
-                    const int lo = b.lb - wmax;
-                    if (lo > b.hi) continue;
-                    if (pt[p] < 0) known = false;
-                    wk += static_cast<unsigned long long>(max(pt[p], 0)) * static_cast<unsigned>(b.hi - max(lo, 0) + 1);
-                }
-                const int uwp = P->T * P->J;
-                const long long npx = static_cast<long long>(max(0, min(h, tc.i0 + P->rows_n) - max(0, tc.i0))) *
-                                      max(0, min(w, tc.j0 + uwp) - max(0, tc.j0));
-                if (known && wk) atomicAdd(dl.band_work, wk * static_cast<unsigned long long>(npx));
-            }
+            b.hi = hi;
+            b.lb = lb;
+            const_cast<DirectBand*>(P->band)[(t - P->tile_base) * band_slabs(P->rows_n) + sl] = b;
         }
     }
 }
 
 int direct_band_window(const DirectProblemDev& d) {
     if (d.band == nullptr) return 0;
-    const long long b = static_cast<long long>(d.rows_n + d.kh - 1) * (d.T * d.J + d.kw) * 4;
+    const long long b = static_cast<long long>(std::min(d.rows_n, kBandSlabRows) + d.kh - 1) * band_pitch(d.T * d.J, d.kw) * 4;
     return static_cast<int>(std::min<long long>(kBandWinBytes, (b + 1023) & ~1023LL));
 }
 
-int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, cudaStream_t st) {
+int direct_band_slabs(const DirectProblemDev& d) { return band_slabs(d.rows_n); }
+
+int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, int slabs, cudaStream_t st) {
     if (dl.total_tiles <= 0) return MORPH_OK;
     bool any = dl.many != nullptr || dl.single.band != nullptr;
     if (!any) return MORPH_OK;
     win_bytes = std::max(1024, std::min(win_bytes, kBandWinBytes));
+    slabs = std::max(1, slabs);
     // resident CTAs per SM: 8 by threads, fewer when their windows fill shared memory
     const long long per_sm = std::max(1, std::min(8, (220 * 1024) / (win_bytes + 3 * 1024)));
-    long long grid = dl.total_tiles;
+    long long grid = slabs * dl.total_tiles;
     const long long cap = static_cast<long long>(ctx->num_sms) * per_sm;
     if (grid > cap) grid = cap;
     prof_begin(ctx, st, "k_band");
@@ -1118,7 +1227,7 @@ int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, cudaStrea
         MORPH_CUDA_TRY(cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandWinBytes));
         mark_kernels_ready(ctx->device, kGroupBand);
     }
-    k_band<<<static_cast<unsigned>(grid), 256, win_bytes, st>>>(dl, win_bytes);
+    k_band<<<static_cast<unsigned>(grid), 256, win_bytes, st>>>(dl, win_bytes, slabs);
     prof_end(ctx, st);
     ctx->launches += 1;
     MORPH_CUDA_TRY(cudaGetLastError());

@@ -293,7 +293,7 @@ size_t direct_ws_bytes(const morph_image* f) { return planes_bytes(f) + direct_b
 //           to 2048^2, L = 16 / 64 / 256, flat disks and full non-flat SEs
 //           3^2..63^2; 83 % within 1.5x).  The MMAs and accumulations depend
 //           on each unit's level band, which depends on the data; the
-//           estimate takes ceil((0.12 L + max b) / 16) chunks of 16 levels,
+//           estimate takes ceil((0.12 L + max b) / Lc) chunks of Lc levels,
 //           the band of uniformly distributed pixel values;
 //   FFT32 : 70 us + FFT FLOP / 5.55e12;  FFT64: 92 us + FFT FLOP / 7.25e11;
 //   NTT   : 80 us + 1.2 x its own estimate (operations, bytes, CTAs).
@@ -513,7 +513,7 @@ static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int er
     dl.mma_count = ctx->d_mma;
     dl.band_work = ctx->d_mma + 1;
     dl.wait_ns = ctx->wait_ns;
-    rc = launch_band(ctx, dl, direct_band_window(dl.single), st);
+    rc = launch_band(ctx, dl, direct_band_window(dl.single), direct_band_slabs(dl.single), st);
     if (rc) return rc;
     return launch_direct(ctx, dl, st);
 }
@@ -607,7 +607,7 @@ int run_one_dev(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b, int
     dl.mma_count = ctx->d_mma;
     dl.band_work = ctx->d_mma + 1;
     dl.wait_ns = ctx->wait_ns;
-    rc = launch_band(ctx, dl, direct_band_window(dl.single), st);
+    rc = launch_band(ctx, dl, direct_band_window(dl.single), direct_band_slabs(dl.single), st);
     if (rc) return rc;
     return launch_direct(ctx, dl, st);
 }

@@ -227,8 +227,12 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
         for (const auto& d : b->probs)
             if (direct_kind(d) != kind) kind = 0;
         int win = 0;
-        for (const auto& d : b->probs) win = std::max(win, direct_band_window(d));
-        rc = launch_band(ctx, dl, win, st);
+        int slabs = 1;
+        for (const auto& d : b->probs) {
+            win = std::max(win, direct_band_window(d));
+            slabs = std::max(slabs, direct_band_slabs(d));
+        }
+        rc = launch_band(ctx, dl, win, slabs, st);
         if (rc) return rc;
         rc = launch_direct(ctx, dl, st, kind);
         if (rc) return rc;

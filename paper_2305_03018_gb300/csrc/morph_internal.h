@@ -59,7 +59,9 @@ constexpr long long kDirectSplitMinUnits = 2 * 152;   // split two-tile units on
 constexpr int kDirectN = 256;        // MMA N: image rows x grey levels of one chunk
 constexpr int kDirectM = 128;        // MMA M: offset groups x output columns
 constexpr int kDirectLc = 16;        // grey levels per chunk of the N axis when L <= 16 or L > 64 (16 image rows)
-constexpr int kDirectLcBand = 8;     // ... when 16 < L <= 64 (32 image rows)
+constexpr int kDirectLcBand = 8;     // ... when 16 < L <= 64 and L + max b > kDirectNarrowMaxR (32 image rows)
+constexpr int kDirectLcNarrow = 4;   // ... when 16 < L <= 64 and L + max b <= kDirectNarrowMaxR (64 image rows)
+constexpr int kDirectNarrowMaxR = 4095;   // degrees + 1 of 4-level plans fit the 12 bits of a packed run entry
 constexpr int kBandTapsMax = 264;    // taps of the per-unit lower bound on the top degree (16 x 16 cells + origin)
 
 // Per unit of a direct launch: hi = the largest level in the unit's input
@@ -67,8 +69,8 @@ constexpr int kBandTapsMax = 264;    // taps of the per-unit lower bound on the 
 // pixels (-1: none).  A product f(x - y) + b(y) that reaches a top degree has
 // level >= lb - b(y), so the pass of offset groups whose largest offset is
 // wmax contracts only the levels [max(0, lb - wmax), hi] (none when
-// lb - wmax > hi), in chunks of kDirectLc levels from the top: chunk c covers
-// hi - kDirectLc (c + 1) + 1 .. hi - kDirectLc c.
+// lb - wmax > hi), in chunks of Lc levels from the top: chunk c covers
+// hi - Lc (c + 1) + 1 .. hi - Lc c.
 struct DirectBand {
     int hi;
     int lb;
@@ -296,9 +298,11 @@ void direct_fill_band(DirectProblemDev* d, const morph_image* f, DirectBand* ban
 size_t direct_band_bytes(const morph_image* f);
 // per-unit grey-level bands of every problem of a direct launch (before launch_direct, same
 // stream); win_bytes: shared memory per CTA for the unit windows (the largest
-// direct_band_window of the launch's problems; larger windows take a slower path)
-int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, cudaStream_t st);
+// direct_band_window of the launch's problems; larger windows take a slower path);
+// slabs: the largest direct_band_slabs of the launch's problems
+int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, int slabs, cudaStream_t st);
 int direct_band_window(const DirectProblemDev& d);
+int direct_band_slabs(const DirectProblemDev& d);   // band entries per unit (slabs of 32 image rows)
 int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st,
                       const OutAdjust* adj = nullptr);
 // validation, erosion reflection, route choice and (cached) plan of one problem

@@ -121,3 +121,45 @@ def test_constant_image_issues_one_chunk_per_unit(ctx):
     # the band-limited work: every unit's band is the single level 77, so each pixel needs |B|
     # multiply-adds
     assert work == se.taps * 256 * 512
+
+
+def test_four_level_chunks_of_64_row_units(ctx):
+    # 16 < L <= 64 with enough MMAs per accumulation and two waves of units: 64-row units whose
+    # levels come in chunks of 4 and whose running results are packed; ragged bottom and right
+    # edges, a unit whose second 32-row slab lies below the image, dilation and erosion
+    g = wl.rng(806)
+    f = g.integers(0, 64, size=(1, 1100, 2100)).astype(np.uint8)
+    for se in (wl.se_flat_disk(15), wl.se_random(g, 31, 31, 0.7, 7, origin=(3, 17))):
+        info = ctx.plan(torch.from_numpy(f).cuda(), 64, se, method="direct_fp8")
+        assert (info.tile_h, info.level_chunks) == (64, 16), se.name
+        _both_ops(ctx, f, 64, se)
+
+
+def test_batch_mixes_chunk_widths(ctx):
+    # one band launch and one persistent direct launch over problems with 4-, 8- and 16-level
+    # chunks (64-, 32- and 16-row units: two band slabs for the first, one for the others)
+    g = wl.rng(807)
+    probs = [
+        wl.Problem(g.integers(0, 64, size=(1, 1100, 2100)).astype(np.uint8), 64, wl.se_flat_disk(15), "dilate", "4"),
+        wl.Problem(g.integers(0, 32, size=(2, 200, 330)).astype(np.uint8), 32, wl.se_full_random(g, 9, 5), "erode",
+                   "8"),
+        wl.Problem(g.integers(0, 256, size=(1, 150, 260)).astype(np.uint8), 256, wl.se_random(g, 11, 7, 0.5, 20),
+                   "dilate", "16"),
+    ]
+    chunks = [ctx.plan(torch.from_numpy(p.f).cuda(), p.L, p.se, op=0 if p.op == "dilate" else 1,
+                       method="direct_fp8").level_chunks for p in probs]
+    assert chunks == [16, 4, 16]
+    items, outs = [], []
+    for p in probs:
+        ft = torch.from_numpy(p.f).cuda()
+        o = torch.full(ft.shape, -9, dtype=torch.int32, device="cuda")
+        c = torch.full(ft.shape, -9, dtype=torch.int32, device="cuda")
+        items.append((ft, p.L, p.se, p.op, o, c))
+        outs.append((o, c))
+    ctx.run_batch(items, method="direct_fp8")
+    ctx.check()
+    for p, (o, c) in zip(probs, outs):
+        fn = oracle.dilate if p.op == "dilate" else oracle.erode
+        rD, rC = fn(p.f, p.L, p.se.mask, p.se.offset, p.se.origin, nthreads=0)
+        assert np.array_equal(o.cpu().numpy(), rD), p.name
+        assert np.array_equal(c.cpu().numpy(), rC), p.name

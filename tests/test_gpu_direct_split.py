@@ -6,7 +6,7 @@ together: tile 1 reads the same staged B blocks as tile 0 shifted by J bytes.
 The cases cover J = 64 and 32 (two and four offset groups), ragged right edges
 where tile 1 of the last unit lies partly or wholly outside the image,
 erosion, and a batch that mixes unit kinds in one launch.  With J = 128 (one
-group) and L > 16 the two tiles' running results of 32 image rows would
+group) and L > 16 the two tiles' running results of 32 or 64 image rows would
 overflow the kernel's per-unit buffer, so those windows run as single-tile
 units, also checked here.
 """
@@ -54,7 +54,7 @@ def _unit(ctx, f, L, se, op=0):
 CASES = [
     ("J128 flat 9x9, single tiles", (2, 600, 700), 64, lambda g: wl.se_flat_square(9), (1, 128, 1, 2)),
     ("J128 flat 9x9, ragged", (4, 300, 600), 64, lambda g: wl.se_flat_square(9), (1, 128, 1, 2)),
-    ("J64 two levels, kw 95", (2, 800, 1000), 32, lambda g: wl.se_random(g, 3, 95, 0.7, 1, origin=(1, 40)),
+    ("J64 two levels, kw 95", (2, 1600, 1000), 32, lambda g: wl.se_random(g, 3, 95, 0.7, 1, origin=(1, 40)),
      (2, 64, 2, 2)),
     ("J32 four levels, kw 99", (1, 160, 2000), 16, lambda g: wl.se_random(g, 3, 99, 0.7, 3, origin=(2, 70)),
      (4, 32, 2, 2)),
@@ -109,7 +109,7 @@ def test_batch_mixes_unit_kinds(ctx):
                    "erode", "packed"),
         wl.Problem(g.integers(0, 16, size=(1, 100, 500)).astype(np.uint8), 16, wl.se_flat_square(9), "dilate",
                    "single"),
-        wl.Problem(g.integers(0, 32, size=(2, 800, 1000)).astype(np.uint8), 32,
+        wl.Problem(g.integers(0, 32, size=(2, 1600, 1000)).astype(np.uint8), 32,
                    wl.se_random(g, 3, 95, 0.7, 1, origin=(1, 40)), "erode", "split J64"),
     ]
     kinds = [_unit(ctx, p.f, p.L, p.se, 0 if p.op == "dilate" else 1)[2:] for p in probs]

@@ -171,7 +171,8 @@ def test_model_matches_the_library_plan(nlev):
     for kw in list(range(1, 70, 3)) + [100, 130, 200, 257, 400, 512]:
         info = _plan(kw, nlev)
         J, ks, nb, T = info.tile_w, info.k_steps, info.unit_blocks, info.unit_tiles
-        # L = 64: units of 32 image rows x 8-level chunks, 8 of them when a band holds every level
+        # L = 64: units of 32 image rows x 8-level chunks (64 x 4 where an accumulation has enough
+        # MMAs, which a one-row SE never has), 8 of them when a band holds every level
         assert info.groups * J == 128 and info.tile_h == 32 and info.level_chunks == 8
         assert ks == (J + kw - 1 + 31) // 32
         nk = (J + kw - 1 + 127) // 128
