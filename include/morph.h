@@ -135,10 +135,12 @@ typedef struct {
     int unit_blocks;         /* direct route: 128-byte K blocks of image planes staged per SE row
                                 and unit (two tiles share them) */
     int k_steps;             /* direct route: 32-column K steps per SE row and tile */
-    int level_chunks;        /* direct route: chunks of 16 grey levels a unit contracts when its
-                                band holds every level (est_flop counts that many); a unit's
-                                band usually needs fewer */
+    int level_chunks;        /* direct route: chunks of grey levels (4, 8 or 16 levels each) a
+                                unit contracts when its band holds every level (est_flop counts
+                                that many); a unit's band usually needs fewer */
     int ring_stages;         /* direct route: stages of the kernel's shared-memory operand ring */
+    int unit_queue;          /* direct route: units the kernel's producer may publish ahead of
+                                its MMA issuer and epilogue */
 } morph_plan_info;
 
 /* --------------------------------------------------------------- calls */

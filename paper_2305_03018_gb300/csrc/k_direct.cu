@@ -69,17 +69,23 @@ constexpr int kDirectNarrowMinMmas = 96;       // MMAs per accumulation below wh
 constexpr int kDirectThreads = 192;
 constexpr uint32_t kTmemCols = 2 * kDirectN;   // two accumulators
 
+constexpr int kUnitQ = 4;                      // units the producer may publish ahead of the consumers
+
 struct DirectSmemTail {
     uint64_t full[kStages];
     uint64_t empty[kStages];
     uint64_t tfull[2];
     uint64_t tempty[2];
+    uint64_t ufull[kUnitQ];                    // unit queue: published by the producer
+    uint64_t uempty[kUnitQ];                   // ... read by the MMA issuer and the epilogue
+    long long unit[kUnitQ];                    // unit index, -1: no more units
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
 };
 
 int direct_stages() { return kStages; }
+int direct_unit_queue() { return kUnitQ; }
 int direct_smem_bytes(int stages) {
     return 1024 + stages * kStageBytes + kRedEntries * 4 + kRunEntries * 8 + static_cast<int>(sizeof(DirectSmemTail));
 }
@@ -219,6 +225,10 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
             mbar_init(smem_u32(&tail->tfull[b]), 1);
             mbar_init(smem_u32(&tail->tempty[b]), 4);
         }
+        for (int q = 0; q < kUnitQ; ++q) {
+            mbar_init(smem_u32(&tail->ufull[q]), 1);
+            mbar_init(smem_u32(&tail->uempty[q]), 2);
+        }
         mbar_init(smem_u32(&tail->drain), 1);
         tail->abort = 0;
         fence_mbar_init();
@@ -238,7 +248,23 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         const uint32_t ring0 = smem_u32(base);
         uint32_t it = 0;
         bool ok = true;
-        for (long long t = blockIdx.x; ok && t < dl.total_tiles; t += gridDim.x) {
+        // units: each CTA's first is its index, later ones are claimed from the launch's counter
+        // (in launch order where there is none); each is published to the MMA issuer and the
+        // epilogue through the unit queue, and -1 ends their loops
+        uint32_t uq = 0;
+        long long t = blockIdx.x;
+        while (ok) {
+            {
+                const uint32_t qs = uq % kUnitQ, qph = (uq / kUnitQ) & 1u;
+                if (!mbar_wait(smem_u32(&tail->uempty[qs]), qph ^ 1u, abort_flag, dl.err, wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                tail->unit[qs] = t < dl.total_tiles ? t : -1;
+                mbar_arrive(smem_u32(&tail->ufull[qs]));
+                ++uq;
+            }
+            if (t >= dl.total_tiles) break;
             const DirectProblemDev* P = direct_find(dl, t);
             if (dl.many != nullptr) {
                 tma_fence_acquire_desc(&P->tmA);
@@ -274,6 +300,8 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 }
               }
             }
+            t = dl.next_unit != nullptr ? static_cast<long long>(gridDim.x) + static_cast<long long>(atomicAdd(dl.next_unit, 1ull))
+                                        : t + gridDim.x;
         }
         // drain, on every exit: the copies already issued land before the CTA may exit, also when
         // another role gave up while this loop ran to its end (in the normal course they have
@@ -297,7 +325,17 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         uint32_t next_slot = 0;
         unsigned long long n_mma = 0;    // MMAs this thread issued (measurement hook)
         bool ok = true;
-        for (long long t = blockIdx.x; ok && t < dl.total_tiles; t += gridDim.x) {
+        uint32_t uq = 0;                 // units read from the unit queue
+        while (ok) {
+            const uint32_t qs = uq % kUnitQ, qph = (uq / kUnitQ) & 1u;
+            if (!mbar_wait(smem_u32(&tail->ufull[qs]), qph, abort_flag, dl.err, wait_ns)) {
+                ok = false;
+                break;
+            }
+            const long long t = tail->unit[qs];
+            mbar_arrive(smem_u32(&tail->uempty[qs]));
+            ++uq;
+            if (t < 0) break;
             const DirectProblemDev* P = direct_find(dl, t);
             const int* rb = P->meta;
             const bool two = (TT == 0) ? (P->T == 2) : (TT >= 2);
@@ -401,7 +439,15 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         uint32_t use0 = 0u, use1 = 0u;   // same slot-claim sequence as the MMA issuer
         uint32_t next_slot = 0;
         unsigned long long band_wk = 0;  // band-limited multiply-adds of this CTA's units (measurement hook)
-        for (long long t = blockIdx.x; t < dl.total_tiles; t += gridDim.x) {
+        uint32_t uq = 0;                 // units read from the unit queue
+        while (true) {
+            const uint32_t qs = uq % kUnitQ, qph = (uq / kUnitQ) & 1u;
+            const bool okq = mbar_wait(smem_u32(&tail->ufull[qs]), qph, abort_flag, dl.err, wait_ns);
+            const long long t = okq ? tail->unit[qs] : -1;
+            if (epi_any_failed(!okq)) break;           // also: every lane has read the slot
+            if (et == 0) mbar_arrive(smem_u32(&tail->uempty[qs]));
+            ++uq;
+            if (t < 0) break;
             const DirectProblemDev* P = direct_find(dl, t);
             const TileCoord tc = direct_tile(P, t);
             const int J = P->J, G = P->G, rows_n = P->rows_n, Lc = P->Lc, T = (TT == 0) ? P->T : (TT == 3 ? 2 : TT);
@@ -928,12 +974,18 @@ void direct_fill_band(DirectProblemDev* d, const morph_image* f, DirectBand* ban
     d->batch_stride = f->batch_stride;
 }
 
-size_t direct_band_bytes(const morph_image* f) {
+static size_t band_entry_bytes(const morph_image* f) {
     // units are rows_n >= 16 image rows by at least 16 columns, with one entry per 32-row slab:
     // at most one entry per 16 image rows, or two for a 64-row unit over an image of <= 16 rows
     const size_t rows = std::max<size_t>((f->h + 15) / 16, 2);
     const size_t units = static_cast<size_t>(f->n) * rows * ((f->w + 15) / 16);
     return (units * sizeof(DirectBand) + 255) & ~size_t(255);
+}
+
+size_t direct_band_bytes(const morph_image* f) { return band_entry_bytes(f) + 256; }
+
+unsigned long long* direct_unit_counter(DirectBand* band, const morph_image* f) {
+    return reinterpret_cast<unsigned long long*>(reinterpret_cast<uint8_t*>(band) + band_entry_bytes(f));
 }
 
 // ------------------------------------------------------------ level bands
@@ -1118,6 +1170,7 @@ __global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectL
     __shared__ __align__(8) int s_toff[kBandTapsMax];
     __shared__ __align__(8) __half2 s_tw[kBandTapsMax];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    if (dl.next_unit != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *dl.next_unit = 0ull;   // for the direct kernel
     for (long long it = blockIdx.x; it < slabs * dl.total_tiles; it += gridDim.x) {
         const int sl = static_cast<int>(it / dl.total_tiles);
         const long long t = it - sl * dl.total_tiles;

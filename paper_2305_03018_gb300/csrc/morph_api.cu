@@ -512,6 +512,7 @@ static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int er
     dl.err = ctx->d_err;
     dl.mma_count = ctx->d_mma;
     dl.band_work = ctx->d_mma + 1;
+    dl.next_unit = dl.single.band != nullptr ? direct_unit_counter(band, f) : nullptr;
     dl.wait_ns = ctx->wait_ns;
     rc = launch_band(ctx, dl, direct_band_window(dl.single), direct_band_slabs(dl.single), st);
     if (rc) return rc;
@@ -606,6 +607,7 @@ int run_one_dev(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b, int
     dl.err = ctx->d_err;
     dl.mma_count = ctx->d_mma;
     dl.band_work = ctx->d_mma + 1;
+    dl.next_unit = dl.single.band != nullptr ? direct_unit_counter(band, f) : nullptr;
     dl.wait_ns = ctx->wait_ns;
     rc = launch_band(ctx, dl, direct_band_window(dl.single), direct_band_slabs(dl.single), st);
     if (rc) return rc;
@@ -740,6 +742,7 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         out->k_steps = d.ksteps;
         out->level_chunks = (d.L + d.Lc - 1) / std::max(1, d.Lc);
         out->ring_stages = direct_stages();
+        out->unit_queue = direct_unit_queue();
         out->groups = d.G;
         out->passes = d.n_pass;
         out->tile_w = d.J;

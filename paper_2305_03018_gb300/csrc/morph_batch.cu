@@ -232,6 +232,14 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
             win = std::max(win, direct_band_window(d));
             slabs = std::max(slabs, direct_band_slabs(d));
         }
+        // the launch's unit counter: in the band buffer of its first problem with bands (the band
+        // kernel, which zeroes it, runs only when some problem has bands)
+        dl.next_unit = nullptr;
+        for (size_t k = 0; k < b->probs.size() && dl.next_unit == nullptr; ++k)
+            if (b->probs[k].band != nullptr) {
+                const auto& it = b->items[b->direct_order[k]];
+                dl.next_unit = direct_unit_counter(reinterpret_cast<DirectBand*>(ws + it.band_off), &it.f);
+            }
         rc = launch_band(ctx, dl, win, slabs, st);
         if (rc) return rc;
         rc = launch_direct(ctx, dl, st, kind);

@@ -112,7 +112,9 @@ struct DirectLaunch {
     long long total_tiles;
     unsigned int* err;
     unsigned long long* mma_count;   // nullable: MMAs issued, added once per CTA
-    unsigned long long* band_work;   // nullable: multiply-adds of the band-limited contraction (band kernel)
+    unsigned long long* band_work;   // nullable: multiply-adds of the band-limited contraction (direct kernel)
+    unsigned long long* next_unit;   // nullable: units claimed after each CTA's first (zeroed by the band kernel);
+                                     // nullptr: CTA b takes units b, b + grid, ...
     unsigned long long wait_ns;      // limit of each bounded wait; 0 = kWaitLimitNs
 };
 
@@ -284,6 +286,7 @@ int direct_kind(const DirectProblemDev& d);
 int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_kind = -1);
 int direct_smem_bytes(int stages);
 int direct_stages();
+int direct_unit_queue();   // slots of the direct kernel's unit queue
 void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,
                          int32_t* out_cnt, long long tile_base, int* status);
 // device-resident SE offsets: plan (metadata and mask on the device), the per-call Toeplitz
@@ -294,8 +297,11 @@ int launch_toeplitz_dev(morph_ctx* ctx, const DirectPlan& p, const int32_t* dev_
                         CUtensorMap* tmA, cudaStream_t st);
 // the image and the per-unit band buffer of a problem (band may be nullptr: every level)
 void direct_fill_band(DirectProblemDev* d, const morph_image* f, DirectBand* band);
-// bytes of the per-unit band buffer for an image of this shape (any plan)
+// bytes of the per-unit band buffer for an image of this shape (any plan), the launch's
+// unit counter included
 size_t direct_band_bytes(const morph_image* f);
+// the unit counter in a band buffer of this image
+unsigned long long* direct_unit_counter(DirectBand* band, const morph_image* f);
 // per-unit grey-level bands of every problem of a direct launch (before launch_direct, same
 // stream); win_bytes: shared memory per CTA for the unit windows (the largest
 // direct_band_window of the launch's problems; larger windows take a slower path);

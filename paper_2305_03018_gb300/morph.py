@@ -67,7 +67,8 @@ class morph_plan_info(ctypes.Structure):
                 ("passes", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
                 ("est_flop", ctypes.c_double), ("workspace_bytes", ctypes.c_size_t),
                 ("unit_tiles", ctypes.c_int), ("unit_blocks", ctypes.c_int),
-                ("k_steps", ctypes.c_int), ("level_chunks", ctypes.c_int), ("ring_stages", ctypes.c_int)]
+                ("k_steps", ctypes.c_int), ("level_chunks", ctypes.c_int), ("ring_stages", ctypes.c_int),
+                ("unit_queue", ctypes.c_int)]
 
 
 class morph_problem(ctypes.Structure):

@@ -173,8 +173,9 @@ def test_workspace_size_matches_plan_and_is_host_only(bwd_chunks):
         for op in (0, 1):
             ws = ctx.workspace_size(f, 64, se, op=op, method=method)
             assert ws == ctx.plan(f, 64, se, op=op, method=method).workspace_bytes, (method, op)
-    # planes n h L round32(w + 31), then one (hi, lb) pair per 16 image rows x 16 columns
-    band = -(-2 * 13 * 19 * 8 // 256) * 256
+    # planes n h L round32(w + 31), then one (hi, lb) pair per 16 image rows x 16 columns and the
+    # launch's unit counter
+    band = -(-2 * 13 * 19 * 8 // 256) * 256 + 256
     assert ctx.workspace_size(f, 64, se, op=0, method="direct_fp8") == 2 * 200 * 64 * 352 + band
     # backward: one float share per pixel (rounded to 256 B) plus one partial sum per (tap, chunk)
     ntaps = int(np.count_nonzero(se.mask))

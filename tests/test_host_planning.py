@@ -32,8 +32,8 @@ def _ws(im, se, op, method="auto"):
 
 def _band_bytes(n, h, w):
     # one (hi, lb) int pair per 16 image rows (two at least: a 64-row unit has two 32-row slabs)
-    # by 16 columns, 256-byte rounded
-    return -(-n * max(-(-h // 16), 2) * -(-w // 16) * 8 // 256) * 256
+    # by 16 columns, 256-byte rounded, then 256 bytes for the launch's unit counter
+    return -(-n * max(-(-h // 16), 2) * -(-w // 16) * 8 // 256) * 256 + 256
 
 
 def test_direct_and_backward_sizes_follow_their_layouts(bwd_chunks):

@@ -9,7 +9,8 @@ its invariants for every window width the planner can produce:
   is issued exactly once, and the row stages ceil((J + 32 ksteps) / 128)
   blocks;
 * the stage ring (STAGES slots, the library's own ring depth, one "landed" and
-  one "consumed" barrier each):
+  one "consumed" barrier each), and the unit queue through which the producer
+  hands each unit to the MMA issuer and the epilogue:
   with split units a stage is released after the next stage's MMAs.  A
   random-interleaving model of the producer, the MMA issuer and the
   asynchronous releases never deadlocks and never lets the producer refill
@@ -44,6 +45,21 @@ def _stages():
     if not _STAGES:
         _STAGES.append(_ring_stages())
     return _STAGES[0]
+
+
+def _unit_queue():
+    """The direct kernel's unit-queue depth as the library reports it."""
+    import ctypes
+
+    from paper_2305_03018_gb300 import morph as M
+    from paper_2305_03018_gb300 import workloads as wl
+    buf = ctypes.create_string_buffer(16)
+    im = M.morph_image()
+    im.data = ctypes.addressof(buf)
+    im.dtype = M.MORPH_U8
+    im.n, im.h, im.w, im.row_stride, im.batch_stride, im.L = 1, 64, 64, 64, 64 * 64, 16
+    sv = M.se_view(wl.se_flat_square(3))
+    return M.morph_plan_query(None, im, sv.c, 0, M.make_opts("direct_fp8")).unit_queue
 
 
 def split_schedule(J, ksteps):
@@ -193,12 +209,14 @@ def test_model_matches_the_library_plan(nlev):
 # ------------------------------------------------------------------ abort path
 def _abort_model(n_units, blocks_per_unit, seed, inject_p, always_drain=True):
     """The three roles of k_direct_fp8 (one tile per unit, accumulator slots used
-    alternately) with one injected wait timeout at a random blocked wait.  Waits
+    alternately) with one injected wait timeout at a random blocked wait.  The
+    producer publishes each unit (then -1) through the unit queue, whose slot is
+    free again once the MMA issuer and the epilogue have both read it.  Waits
     fail once the CTA's abort flag is up.  Copies land in any order; MMA batches
     complete in issue order, each then arriving on its barrier.  Returns the
     copies and MMA batches still in flight when all roles reach the final barrier
     (after which TMEM is freed and the CTA exits), or raises on a deadlock."""
-    STAGES = _stages()
+    STAGES, Q = _stages(), _unit_queue()
     rnd = random.Random(seed)
     st = {"abort": False, "injected": False}
     landed = set()            # copy ids that have landed
@@ -208,7 +226,9 @@ def _abort_model(n_units, blocks_per_unit, seed, inject_p, always_drain=True):
     tfull = [0, 0]            # accumulator-full arrivals per TMEM slot
     tempty = [0, 0]           # accumulator-free arrivals per TMEM slot (epilogue)
     drained = [False]
-    program = [(u, kc) for u in range(n_units) for kc in range(blocks_per_unit)]
+    ufull = [0] * Q           # units published per queue slot
+    uread = [0] * Q           # reader arrivals per queue slot (two per publication)
+    uval = [None] * Q
 
     def wait(cond):
         while not cond():
@@ -220,23 +240,48 @@ def _abort_model(n_units, blocks_per_unit, seed, inject_p, always_drain=True):
             yield None
         return True
 
+    def read_unit(uq):
+        q = uq % Q
+        ok = yield from wait(lambda: ufull[q] > uq // Q)
+        if not ok:
+            return False, None
+        t = uval[q]
+        assert t == (uq if uq < n_units else -1), "a reader saw another publication of the slot"
+        uread[q] += 1
+        return True, t
+
     def producer():
         it, ok = 0, True
-        for _ in program:
-            s = it % STAGES
-            ok = yield from wait(lambda: released[s] >= it // STAGES)
+        for u in range(n_units + 1):
+            q = u % Q
+            ok = yield from wait(lambda: uread[q] >= 2 * (u // Q))
             if not ok:
                 break
-            inflight_copies.add(it)
-            it += 1
+            uval[q] = u if u < n_units else -1
+            ufull[q] += 1
+            if u == n_units:
+                break
+            for kc in range(blocks_per_unit):
+                s = it % STAGES
+                ok = yield from wait(lambda: released[s] >= it // STAGES)
+                if not ok:
+                    break
+                inflight_copies.add(it)
+                it += 1
+            if not ok:
+                break
         if always_drain or not ok:
             for k in range(max(0, it - STAGES), it):
                 while k in inflight_copies:
                     yield None
 
     def mma():
-        it, use, nxt, ok = 0, [0, 0], 0, True
-        for u in range(n_units):
+        it, use, nxt, ok, uq = 0, [0, 0], 0, True, 0
+        while True:
+            ok, t = yield from read_unit(uq)
+            uq += 1
+            if not ok or t < 0:
+                break
             s0, nxt = nxt, nxt ^ 1
             ok = yield from wait(lambda: tempty[s0] >= use[s0])
             if not ok:
@@ -258,8 +303,12 @@ def _abort_model(n_units, blocks_per_unit, seed, inject_p, always_drain=True):
                 yield None
 
     def epilogue():
-        use, nxt = [0, 0], 0
-        for u in range(n_units):
+        use, nxt, uq = [0, 0], 0, 0
+        while True:
+            ok, t = yield from read_unit(uq)
+            uq += 1
+            if not ok or t < 0:
+                break
             s0, nxt = nxt, nxt ^ 1
             ok = yield from wait(lambda: tfull[s0] > use[s0])
             if not ok:
@@ -293,6 +342,8 @@ def _abort_model(n_units, blocks_per_unit, seed, inject_p, always_drain=True):
                     next(roles[r])
                 except StopIteration:
                     done[r] = True
+    if not st["abort"]:
+        assert tempty == tfull and sum(tfull) == n_units, "a unit was not completed"
     return len(inflight_copies), len(mma_q)
 
 
@@ -301,12 +352,20 @@ def test_abort_drains_every_copy_and_mma_before_exit():
     # can still land in shared memory and no MMA can still write TMEM
     hits = 0
     for trial in range(600):
-        n_units = 1 + trial % 5
-        blocks = 1 + (trial // 5) % 4
+        n_units = 1 + trial % 9                 # up to twice the unit queue
+        blocks = 1 + (trial // 9) % 4
         copies, mmas = _abort_model(n_units, blocks, trial, inject_p=0.02)
         assert copies == 0 and mmas == 0, (trial, copies, mmas)
         hits += 1
     assert hits == 600
+
+
+def test_unit_queue_completes_every_unit_without_a_timeout():
+    # no injected timeout: every unit passes through the queue and the accumulators, in any
+    # interleaving, and nothing is in flight at the end
+    for trial in range(300):
+        copies, mmas = _abort_model(1 + trial % 12, 1 + trial % 3, 7000 + trial, inject_p=0.0)
+        assert copies == 0 and mmas == 0
 
 
 def test_abort_model_catches_a_drain_taken_only_by_the_role_that_failed():
