@@ -50,6 +50,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
 
 #include "morph_internal.h"
@@ -812,7 +813,24 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
             bt.insert(bt.end(), {0, 0, dev ? -(t0 + 1) : static_cast<int>(se->offset[t0])});
         }
         p->n_band_taps = static_cast<int>(bt.size() / 3);
+        p->n_band_segs = 0;
+        if (!dev && p->n_band_taps > 0) {
+            // taps in runs of equal offset (largest first): the band kernel takes each run's
+            // maximum level and adds the run's offset once; segment ends follow the taps in meta
+            std::vector<std::array<int, 3>> tv(p->n_band_taps);
+            for (int k = 0; k < p->n_band_taps; ++k) tv[k] = {bt[3 * k], bt[3 * k + 1], bt[3 * k + 2]};
+            std::stable_sort(tv.begin(), tv.end(), [](const auto& x, const auto& y) { return x[2] > y[2]; });
+            for (int k = 0; k < p->n_band_taps; ++k)
+                for (int e = 0; e < 3; ++e) bt[3 * k + e] = tv[k][e];
+        }
         p->meta.insert(p->meta.end(), bt.begin(), bt.end());
+        p->band_seg_off = static_cast<int>(p->meta.size());
+        if (!dev)
+            for (int k = 1; k <= p->n_band_taps; ++k)
+                if (k == p->n_band_taps || bt[3 * k + 2] != bt[3 * (k - 1) + 2]) {
+                    p->meta.push_back(k);
+                    ++p->n_band_segs;
+                }
     }
     // taps of each pass (the band-limited work count), -1 when the offsets are on the device
     p->pass_taps_off = static_cast<int>(p->meta.size());
@@ -938,6 +956,8 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
     d->kh = p.kh;
     d->band_tap_off = p.band_tap_off;
     d->n_band_taps = p.n_band_taps;
+    d->band_seg_off = p.band_seg_off;
+    d->n_band_segs = p.n_band_segs;
     d->pass_taps_off = p.pass_taps_off;
     d->band = nullptr;
     d->dev_off = nullptr;
@@ -1009,6 +1029,7 @@ __device__ __forceinline__ int band_pixel(const void* src, int dtype, long long 
 
 constexpr int kBandWinBytes = 96 * 1024;   // shared-memory window of a unit, 4 B per position
 constexpr int kBandPairs = 8;              // pixel pairs per thread (32 rows x 128 columns / 2 / 256 threads)
+constexpr int kBandCtasPerSm = 3;          // resident CTAs per SM the registers allow (80 per thread)
 constexpr int kBandWMax = 1024;            // offsets above this are lowered to it for the bound (fp16-exact sums)
 
 // Offset of a lower-bound tap: stored in the plan, or (v < 0) the device-resident
@@ -1101,12 +1122,16 @@ union BandH2 {
 
 // The thread's minimum over its NP pixel pairs of the subset maximum: pair k of
 // thread t is pair t + 256 k of the slab, row-major (uw / 2 pairs per row).
-// Two accumulators per pair take alternate taps, so consecutive taps do not
-// wait on each other; a tap pair's offsets and offsets' weights are read with
-// one 8-byte load each.
+// With nseg > 0 the taps come in nseg runs of one offset (ends in s_seg): a run
+// takes the maximum level over its taps and adds its offset once.  Otherwise
+// (offsets on the device, in box order) each tap adds its own offset; two
+// accumulators per pair take alternate taps, so consecutive taps do not wait
+// on each other, and a tap pair's offsets and weights are read with one 8-byte
+// load each.
 template <int NP>
 __device__ __forceinline__ int band_lower(const DirectProblemDev* P, const TileCoord& tc, const __half2* q,
-                                          const int* s_toff, const __half2* s_tw, int ntap, int WQ, int npair) {
+                                          const int* s_toff, const __half2* s_tw, const int* s_seg, int nseg,
+                                          int ntap, int WQ, int npair) {
     const int uw = P->T * P->J, half_w = uw >> 1, sh = __ffs(half_w) - 1;
     const int ps = band_pair_stride(uw), psh = __ffs(ps) - 1;
     if (static_cast<int>(threadIdx.x) >= npair) return 0x7fffffff;   // (NP == 1 with fewer pairs than threads)
@@ -1121,6 +1146,29 @@ __device__ __forceinline__ int band_lower(const DirectProblemDev* P, const TileC
         const int j = ((c >> psh) << (psh + 1)) + (c & (ps - 1));
         base[k] = (pr + P->kh - 1 - P->oy) * WQ + j + P->kw - 1 - P->ox;
     }
+    if (nseg > 0) {
+        // a1 holds the result so far; a0 the current run's maximum level (-4096: no tap inside)
+        int s = 0;
+        for (int g = 0; g < nseg; ++g) {
+            const int e = s_seg[g];
+            const __half2 wg = s_tw[s];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) a0[k] = __floats2half2_rn(-4096.f, -4096.f);
+            for (; s + 1 < e; s += 2) {
+                const int o0 = s_toff[s], o1 = s_toff[s + 1];
+#pragma unroll
+                for (int k = 0; k < NP; ++k) a0[k] = __hmax2(a0[k], __hmax2(q[base[k] + o0], q[base[k] + o1]));
+            }
+            if (s < e) {
+                const int o0 = s_toff[s];
+#pragma unroll
+                for (int k = 0; k < NP; ++k) a0[k] = __hmax2(a0[k], q[base[k] + o0]);
+                ++s;
+            }
+#pragma unroll
+            for (int k = 0; k < NP; ++k) a1[k] = __hmax2(a1[k], __hadd2(a0[k], wg));
+        }
+    } else {
     const int2* toff2 = reinterpret_cast<const int2*>(s_toff);
     const uint2* tw2 = reinterpret_cast<const uint2*>(s_tw);
     int s = 0;
@@ -1142,6 +1190,7 @@ __device__ __forceinline__ int band_lower(const DirectProblemDev* P, const TileC
 #pragma unroll
         for (int k = 0; k < NP; ++k) a0[k] = __hmax2(a0[k], __hadd2(q[base[k] + o0], w0));
     }
+    }
     int lb = 0x7fffffff;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -1156,7 +1205,7 @@ __device__ __forceinline__ int band_lower(const DirectProblemDev* P, const TileC
     return lb;
 }
 
-__global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectLaunch dl, int win_bytes, int slabs) {
+__global__ void __launch_bounds__(256, kBandCtasPerSm) k_band(const __grid_constant__ DirectLaunch dl, int win_bytes, int slabs) {
     // One work item per unit slab (kBandSlabRows image rows of a unit; item s T + t is slab s of
     // unit t, T units in the launch, and units with fewer slabs skip the items past theirs).
     // The slab's input window (rows i - r + oy, columns j - c + ox over the SE box, not clipped)
@@ -1169,6 +1218,7 @@ __global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectL
     __shared__ int s_hi[8], s_lb[8];
     __shared__ __align__(8) int s_toff[kBandTapsMax];
     __shared__ __align__(8) __half2 s_tw[kBandTapsMax];
+    __shared__ int s_seg[kBandTapsMax];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     if (dl.next_unit != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *dl.next_unit = 0ull;   // for the direct kernel
     for (long long it = blockIdx.x; it < slabs * dl.total_tiles; it += gridDim.x) {
@@ -1186,11 +1236,13 @@ __global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectL
         const bool fast = static_cast<long long>(WR) * WQ * 4 <= win_bytes &&
                           rows * (uw >> 1) <= 256 * kBandPairs;      // block-uniform
         __syncthreads();   // the previous item's readers of the shared arrays are done
+        const int nseg = P->n_band_segs;
         for (int k = threadIdx.x; k < ntap; k += blockDim.x) {
             const int* tp = P->meta + P->band_tap_off + 3 * k;
             s_toff[k] = tp[0] * WQ + tp[1];
             const float wv = static_cast<float>(min(band_tap_offset(P, tp[2]), kBandWMax));
             s_tw[k] = __floats2half2_rn(wv, wv);
+            if (k < nseg) s_seg[k] = P->meta[P->band_seg_off + k];
         }
         int hi = -1;
         int lb = 0x7fffffff;
@@ -1208,10 +1260,10 @@ __global__ void __launch_bounds__(256, 4) k_band(const __grid_constant__ DirectL
             // pixel pairs of the slab: rows x uw / 2 pairs per row, npair / 256 per thread
             // (a power of two; with fewer pairs than threads, one pair for the first npair threads)
             const int npair = rows * (uw >> 1);
-            if (npair <= 256) lb = band_lower<1>(P, tc, q, s_toff, s_tw, ntap, WQ, npair);
-            else if (npair <= 512) lb = band_lower<2>(P, tc, q, s_toff, s_tw, ntap, WQ, npair);
-            else if (npair <= 1024) lb = band_lower<4>(P, tc, q, s_toff, s_tw, ntap, WQ, npair);
-            else lb = band_lower<8>(P, tc, q, s_toff, s_tw, ntap, WQ, npair);
+            if (npair <= 256) lb = band_lower<1>(P, tc, q, s_toff, s_tw, s_seg, nseg, ntap, WQ, npair);
+            else if (npair <= 512) lb = band_lower<2>(P, tc, q, s_toff, s_tw, s_seg, nseg, ntap, WQ, npair);
+            else if (npair <= 1024) lb = band_lower<4>(P, tc, q, s_toff, s_tw, s_seg, nseg, ntap, WQ, npair);
+            else lb = band_lower<8>(P, tc, q, s_toff, s_tw, s_seg, nseg, ntap, WQ, npair);
         } else {
             // windows too large for shared memory (SE boxes of hundreds of rows): direct loads
             const int r0 = max(0, wr0), r1 = min(h, tc.i0 + rows + P->oy);
@@ -1270,8 +1322,8 @@ int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, int slabs
     if (!any) return MORPH_OK;
     win_bytes = std::max(1024, std::min(win_bytes, kBandWinBytes));
     slabs = std::max(1, slabs);
-    // resident CTAs per SM: 8 by threads, fewer when their windows fill shared memory
-    const long long per_sm = std::max(1, std::min(8, (220 * 1024) / (win_bytes + 3 * 1024)));
+    // resident CTAs per SM: kBandCtasPerSm by registers, fewer when their windows fill shared memory
+    const long long per_sm = std::max(1, std::min(kBandCtasPerSm, (220 * 1024) / (win_bytes + 4 * 1024)));
     long long grid = slabs * dl.total_tiles;
     const long long cap = static_cast<long long>(ctx->num_sms) * per_sm;
     if (grid > cap) grid = cap;

@@ -91,6 +91,7 @@ struct DirectProblemDev {
     int dtype;
     long long row_stride, batch_stride;
     int kh, maxb, band_tap_off, n_band_taps;
+    int band_seg_off, n_band_segs;   // runs of band taps with one offset (0: offsets on the device)
     int pass_taps_off;      // meta offset of the taps per pass (-1 entries: offsets on the device)
     int h, w, nimg, L;
     int Lc, rows_n, J, G;
@@ -121,6 +122,7 @@ struct DirectLaunch {
 struct DirectPlan {
     int L = 0, Lc = 0, rows_n = 0, J = 0, G = 0, n_pass = 0, nk = 0, ksteps = 0, T = 1, split = 0, nb = 0;
     int band_tap_off = 0, n_band_taps = 0;   // lower-bound taps (oy - r, ox - c, b) in meta
+    int band_seg_off = 0, n_band_segs = 0;   // ends of their runs of equal b (host offsets only)
     int pass_taps_off = 0;                    // taps of each pass in meta
     int kh = 0, kw = 0, oy = 0, ox = 0, e = 0, erode = 0, shift = 0;
     int h = 0, w = 0, nimg = 0, w_pad = 0;
