@@ -62,10 +62,11 @@ constexpr int kStages = 3;
 constexpr int kStageA = 128 * 128;             // 16 KB: 128 Toeplitz rows x 128 B of K
 constexpr int kStageB = kDirectN * 128;        // 32 KB: 256 (row, level) rows x 128 B of K
 constexpr int kStageBytes = kStageA + kStageB;
-constexpr int kRedEntries = 2 * 32 * 128;      // rows_n x 128 lanes, 4 B each; with rows_n <= 32 both tiles of
-                                               // a two-tile unit are read out before either is reduced
+constexpr int kRedEntries = 2 * 64 * 128;      // rows_n x 128 lanes per tile, 4 B each: both tiles of a
+                                               // two-tile unit are read out before either is reduced
 constexpr int kRunEntries = 4096;              // rows_n x J x T (int2: <= 32 x 128, or 16 x 128 x 2)
-constexpr int kRunPacked = 2 * kRunEntries;    // the same 32 KB as packed uint32 entries (4-level plans: 64 x 128)
+constexpr int kRunPacked = 2 * kRunEntries;    // the same as packed uint32 entries (4-level plans: 64 x 128)
+constexpr int kRunWords = kRunPacked / 128;    // 32-bit words of running results per epilogue thread
 constexpr int kDirectNarrowMinMmas = 96;       // MMAs per accumulation below which 4-level plans do not pay
 constexpr int kDirectThreads = 192;
 constexpr uint32_t kTmemCols = 2 * kDirectN;   // two accumulators
@@ -88,7 +89,7 @@ struct DirectSmemTail {
 int direct_stages() { return kStages; }
 int direct_unit_queue() { return kUnitQ; }
 int direct_smem_bytes(int stages) {
-    return 1024 + stages * kStageBytes + kRedEntries * 4 + kRunEntries * 8 + static_cast<int>(sizeof(DirectSmemTail));
+    return 1024 + stages * kStageBytes + kRedEntries * 4 + static_cast<int>(sizeof(DirectSmemTail));
 }
 
 __device__ __forceinline__ const DirectProblemDev* direct_find(const DirectLaunch& dl, long long t) {
@@ -204,13 +205,9 @@ template <int TT>
 __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_constant__ DirectLaunch dl) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    // red: one lane's result of one image row of one chunk (epi_read_rows); run: (degree, count)
-    // so far per output pixel, as int2, or packed (degree + 1) << 20 | count in 4-level plans,
-    // whose degrees stay below L + max b <= kDirectNarrowMaxR
+    // red: one lane's result of one image row of one chunk (epi_read_rows)
     uint32_t* red = reinterpret_cast<uint32_t*>(base + kStages * kStageBytes);
-    int2* run = reinterpret_cast<int2*>(red + kRedEntries);
-    uint32_t* runp = reinterpret_cast<uint32_t*>(run);
-    DirectSmemTail* tail = reinterpret_cast<DirectSmemTail*>(run + kRunEntries);
+    DirectSmemTail* tail = reinterpret_cast<DirectSmemTail*>(red + kRedEntries);
     volatile int* abort_flag = &tail->abort;
     const unsigned long long wait_ns = dl.wait_ns != 0ull ? dl.wait_ns : kWaitLimitNs;
 
@@ -441,6 +438,11 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         uint32_t next_slot = 0;
         unsigned long long band_wk = 0;  // band-limited multiply-adds of this CTA's units (measurement hook)
         uint32_t uq = 0;                 // units read from the unit queue
+        // the running (degree, count) of this thread's pixels across a unit's accumulations (pixel
+        // et + 128 k of the unit's T tiles in word k): packed (degree + 1) << 20 | count in 4-level
+        // plans, whose degrees stay below L + max b <= kDirectNarrowMaxR, else an int2 in words
+        // 2 k, 2 k + 1; thread-private memory, so the shared memory holds one more ring stage
+        uint32_t runl[kRunWords];
         while (true) {
             const uint32_t qs = uq % kUnitQ, qph = (uq / kUnitQ) & 1u;
             const bool okq = mbar_wait(smem_u32(&tail->ufull[qs]), qph, abort_flag, dl.err, wait_ns);
@@ -496,45 +498,87 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 const int pairs = rows_n * J;
                 const int* gwp = gw + p * 8;
                 const bool packed = Lc == kDirectLcNarrow;
+                // quads of four pixels of one row per thread and step: one 16-byte shared load per
+                // group, 16-byte output stores where the row allows them
+                const int jsh = __ffs(J) - 1;                   // J is a power of two >= 16
+                const int kq = (pairs + 511) >> 9;              // quads per thread per tile, at most
+                const int h = P->h, w = P->w, outv = P->erode ? P->L - 1 : 0, sgn = P->erode ? -1 : 1;
                 auto reduce = [&](int tt, int rbase) {
-                    for (int idx = et; idx < pairs; idx += 128) {
-                        const int tr = idx / J, jl = idx - tr * J;
-                        int best = -1, bc = 0;
+                    for (int qd = et, k = 0; qd < (pairs >> 2); qd += 128, ++k) {
+                        const int p0 = qd << 2;
+                        const int tr = p0 >> jsh, jl = p0 & (J - 1);
+                        int best[4] = {-1, -1, -1, -1}, bc[4] = {0, 0, 0, 0};
                         for (int gg = 0; gg < G; ++gg) {
-                            const uint32_t e = red[rbase + tr * 128 + gg * J + jl];
-                            if (e == 0u) continue;
-                            const int deg = lev0 + static_cast<int>(e >> 20) - 1 + gwp[gg];
-                            const int c = static_cast<int>(e & 0xFFFFFu);
-                            if (deg > best) { best = deg; bc = c; }
-                            else if (deg == best) bc += c;
-                        }
-                        int2 cur = make_int2(best, bc);
-                        const int ri = tt * pairs + idx;
-                        if (u > 0) {
-                            int2 prev;
-                            if (packed) {
-                                const uint32_t e = runp[ri];
-                                prev = make_int2(static_cast<int>(e >> 20) - 1, static_cast<int>(e & 0xFFFFFu));
-                            } else {
-                                prev = run[ri];
+                            const uint4 e4 = *reinterpret_cast<const uint4*>(red + rbase + tr * 128 + gg * J + jl);
+                            const uint32_t ev[4] = {e4.x, e4.y, e4.z, e4.w};
+                            const int d0 = lev0 - 1 + gwp[gg];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                if (ev[c] == 0u) continue;
+                                const int deg = d0 + static_cast<int>(ev[c] >> 20);
+                                const int cn = static_cast<int>(ev[c] & 0xFFFFFu);
+                                if (deg > best[c]) { best[c] = deg; bc[c] = cn; }
+                                else if (deg == best[c]) bc[c] += cn;
                             }
-                            if (prev.x > cur.x) cur = prev;
-                            else if (prev.x == cur.x && cur.x >= 0) cur.y += prev.y;
                         }
-                        if (u < n_units - 1) {
-                            if (packed)
-                                runp[ri] = cur.x < 0 ? 0u
-                                                     : (static_cast<uint32_t>(cur.x + 1) << 20) | static_cast<uint32_t>(cur.y);
-                            else
-                                run[ri] = cur;
-                        } else {
+                        const int wq = (tt * kq + k) << 2;              // words of this quad in runl
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            if (u > 0) {
+                                int2 prev;
+                                if (packed) {
+                                    const uint32_t e = runl[wq + c];
+                                    prev = make_int2(static_cast<int>(e >> 20) - 1, static_cast<int>(e & 0xFFFFFu));
+                                } else {
+                                    prev = make_int2(static_cast<int>(runl[2 * (wq + c)]), static_cast<int>(runl[2 * (wq + c) + 1]));
+                                }
+                                if (prev.x > best[c]) { best[c] = prev.x; bc[c] = prev.y; }
+                                else if (prev.x == best[c] && best[c] >= 0) bc[c] += prev.y;
+                            }
+                            if (u < n_units - 1) {
+                                if (packed) {
+                                    runl[wq + c] = best[c] < 0 ? 0u
+                                                               : (static_cast<uint32_t>(best[c] + 1) << 20) | static_cast<uint32_t>(bc[c]);
+                                } else {
+                                    runl[2 * (wq + c)] = static_cast<uint32_t>(best[c]);
+                                    runl[2 * (wq + c) + 1] = static_cast<uint32_t>(bc[c]);
+                                }
+                            }
+                        }
+                        if (u == n_units - 1) {
                             const int i = tc.i0 + tr, j = tc.j0 + tt * J + jl;
-                            if (i < P->h && j >= 0 && j < P->w) {
-                                const int dval = cur.x < 0 ? 0 : cur.x;
-                                const long long o = (static_cast<long long>(tc.n) * P->h + i) * P->w + j;
-                                P->out[o] = (P->erode ? (P->L - 1 - dval) : dval) + P->out_add -
-                                            (P->out_sub ? P->out_sub[o] : 0);
-                                if (P->out_cnt) P->out_cnt[o] = cur.x < 0 ? 0 : cur.y;
+                            if (i < h) {
+                                const long long o = (static_cast<long long>(tc.n) * h + i) * w + j;
+                                int dv[4], cv[4];
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) {
+                                    dv[c] = outv + sgn * (best[c] < 0 ? 0 : best[c]) + P->out_add;
+                                    cv[c] = best[c] < 0 ? 0 : bc[c];
+                                }
+                                int32_t* po = P->out + o;
+                                int32_t* pc = P->out_cnt ? P->out_cnt + o : nullptr;
+                                const int32_t* ps = P->out_sub ? P->out_sub + o : nullptr;
+                                const bool vec = j >= 0 && j + 3 < w && (reinterpret_cast<uintptr_t>(po) & 15u) == 0 &&
+                                                 (pc == nullptr || (reinterpret_cast<uintptr_t>(pc) & 15u) == 0) &&
+                                                 (ps == nullptr || (reinterpret_cast<uintptr_t>(ps) & 15u) == 0);
+                                if (vec) {
+                                    if (ps) {
+                                        const int4 sv = *reinterpret_cast<const int4*>(ps);
+                                        dv[0] -= sv.x;
+                                        dv[1] -= sv.y;
+                                        dv[2] -= sv.z;
+                                        dv[3] -= sv.w;
+                                    }
+                                    *reinterpret_cast<int4*>(po) = make_int4(dv[0], dv[1], dv[2], dv[3]);
+                                    if (pc) *reinterpret_cast<int4*>(pc) = make_int4(cv[0], cv[1], cv[2], cv[3]);
+                                } else {
+#pragma unroll
+                                    for (int c = 0; c < 4; ++c) {
+                                        if (j + c < 0 || j + c >= w) continue;
+                                        po[c] = dv[c] - (ps ? ps[c] : 0);
+                                        if (pc) pc[c] = cv[c];
+                                    }
+                                }
                             }
                         }
                     }
@@ -960,6 +1004,7 @@ void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t
     d->n_band_segs = p.n_band_segs;
     d->pass_taps_off = p.pass_taps_off;
     d->band = nullptr;
+    d->lev_range = nullptr;
     d->dev_off = nullptr;
     d->dev_reflect = 0;
     d->rows_n = p.rows_n;
@@ -988,6 +1033,7 @@ int direct_kind(const DirectProblemDev& d) { return d.split ? 3 : d.T; }
 void direct_fill_band(DirectProblemDev* d, const morph_image* f, DirectBand* band) {
     // with L <= Lc one chunk holds every level: no band to compute
     d->band = f->L > d->Lc ? band : nullptr;
+    d->lev_range = d->band != nullptr ? reinterpret_cast<int*>(direct_unit_counter(band, f) + 1) : nullptr;
     d->src = f->data;
     d->dtype = f->dtype;
     d->row_stride = f->row_stride;
@@ -1333,6 +1379,53 @@ int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, int slabs
         mark_kernels_ready(ctx->device, kGroupBand);
     }
     k_band<<<static_cast<unsigned>(grid), 256, win_bytes, st>>>(dl, win_bytes, slabs);
+    prof_end(ctx, st);
+    ctx->launches += 1;
+    MORPH_CUDA_TRY(cudaGetLastError());
+    return MORPH_OK;
+}
+
+// The levels the direct kernel reads for a problem: unit t's chunks cover at most
+// [max(0, lb - max b) - (Lc - 1), hi] of its band (direct_band), so the union over the
+// units is within [min_t (lb_t - max b - Lc + 1), max_t hi_t]; the encoder writes only those
+// planes (levels outside 0..L-1 are the copy's zero fill).
+__global__ void __launch_bounds__(1024) k_band_range(const __grid_constant__ DirectLaunch dl) {
+    __shared__ int s_lo[32], s_hi[32];
+    const DirectProblemDev* P = dl.many != nullptr ? &dl.many[blockIdx.x] : &dl.single;
+    if (P->band == nullptr || P->lev_range == nullptr) return;      // block-uniform
+    int lo = P->L, hi = -1;
+    for (long long t = P->tile_base + threadIdx.x; t < P->tile_base + P->tiles; t += blockDim.x) {
+        const DirectBand b = direct_band(P, t);
+        lo = min(lo, max(0, b.lb - P->maxb - P->Lc + 1));
+        hi = max(hi, b.hi);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_lo[warp] = lo;
+        s_hi[warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < static_cast<int>(blockDim.x >> 5); ++k) {
+            lo = min(lo, s_lo[k]);
+            hi = max(hi, s_hi[k]);
+        }
+        P->lev_range[0] = lo;
+        P->lev_range[1] = hi;
+    }
+}
+
+int launch_band_range(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st) {
+    if (dl.total_tiles <= 0) return MORPH_OK;
+    if (dl.many == nullptr && dl.single.band == nullptr) return MORPH_OK;
+    const unsigned grid = dl.many != nullptr ? static_cast<unsigned>(dl.nprob) : 1u;
+    prof_begin(ctx, st, "k_band_range");
+    k_band_range<<<grid, 1024, 0, st>>>(dl);
     prof_end(ctx, st);
     ctx->launches += 1;
     MORPH_CUDA_TRY(cudaGetLastError());
