@@ -3,9 +3,10 @@
 // level-major per image row, planes[n][i][v][j], so that the tensor-core route
 // can read a (row, level) x (column window) tile with one TMA box.
 //
-// HBM-bound: 1 pixel read, L bytes written per pixel.  Each thread owns 16
-// consecutive columns of one row and writes one 16-byte vector per level;
-// a warp writes 512 contiguous bytes of one plane.
+// HBM-bound: 1 pixel read, L bytes written per pixel -- or only the planes of
+// the levels the tensor-core route will read, when its band range is known.
+// Each thread owns 16 consecutive columns of one row and writes one 16-byte
+// vector per level; a warp writes 512 contiguous bytes of one plane.
 #include "morph_internal.h"
 #include "ptx.cuh"
 
@@ -65,7 +66,12 @@ __global__ void __launch_bounds__(256) k_encode_planes(const EncodeJob* __restri
         }
         if (bad) atomicOr(err, MORPH_DEVERR_RANGE);
         uint8_t* dst = J->planes + (row * J->L) * (long long)J->w_pad + j0;
-        for (int v = 0; v < J->L; ++v) {
+        int v0 = 0, v1 = J->L - 1;
+        if (J->lev_range != nullptr) {
+            v0 = max(v0, J->lev_range[0]);
+            v1 = min(v1, J->lev_range[1]);
+        }
+        for (int v = v0; v <= v1; ++v) {
             const uint32_t v4 = 0x01010101u * static_cast<uint32_t>(v);
             uint4 q;
             q.x = onehot4(packed[0], valid[0], v4);

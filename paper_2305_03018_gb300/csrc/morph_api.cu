@@ -493,9 +493,8 @@ static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int er
     job.w_pad = dp.w_pad;
     job.shift = dp.shift;
     job.item_base = 0;
+    job.lev_range = nullptr;
     const long long items = static_cast<long long>(f->n) * f->h * (dp.w_pad / 16);
-    rc = launch_encode(ctx, &job, 1, items, nullptr, st);
-    if (rc) return rc;
 
     DirectLaunch dl;
     std::memset(static_cast<void*>(&dl), 0, sizeof(dl));
@@ -515,6 +514,12 @@ static int run_plan(morph_ctx* ctx, const Plan& pl, const morph_image* f, int er
     dl.next_unit = dl.single.band != nullptr ? direct_unit_counter(band, f) : nullptr;
     dl.wait_ns = ctx->wait_ns;
     rc = launch_band(ctx, dl, direct_band_window(dl.single), direct_band_slabs(dl.single), st);
+    if (rc) return rc;
+    // the planes after the bands: only the levels some unit's chunks read are written
+    rc = launch_band_range(ctx, dl, st);
+    if (rc) return rc;
+    job.lev_range = dl.single.lev_range;
+    rc = launch_encode(ctx, &job, 1, items, nullptr, st);
     if (rc) return rc;
     return launch_direct(ctx, dl, st);
 }
@@ -591,8 +596,8 @@ int run_one_dev(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b, int
     job.w_pad = dp.w_pad;
     job.shift = dp.shift;
     job.item_base = 0;
-    rc = launch_encode(ctx, &job, 1, static_cast<long long>(f->n) * f->h * (dp.w_pad / 16), nullptr, st);
-    if (rc) return rc;
+    job.lev_range = nullptr;
+    const long long items = static_cast<long long>(f->n) * f->h * (dp.w_pad / 16);
     DirectLaunch dl;
     std::memset(static_cast<void*>(&dl), 0, sizeof(dl));
     direct_fill_problem(dp, &dl.single, planes, out, cnt, 0, &rc);
@@ -610,6 +615,12 @@ int run_one_dev(morph_ctx* ctx, const morph_image* f, const morph_se_dev* b, int
     dl.next_unit = dl.single.band != nullptr ? direct_unit_counter(band, f) : nullptr;
     dl.wait_ns = ctx->wait_ns;
     rc = launch_band(ctx, dl, direct_band_window(dl.single), direct_band_slabs(dl.single), st);
+    if (rc) return rc;
+    // the planes after the bands: only the levels some unit's chunks read are written
+    rc = launch_band_range(ctx, dl, st);
+    if (rc) return rc;
+    job.lev_range = dl.single.lev_range;
+    rc = launch_encode(ctx, &job, 1, items, nullptr, st);
     if (rc) return rc;
     return launch_direct(ctx, dl, st);
 }

@@ -186,12 +186,13 @@ int batch_descriptors(morph_batch* b, uint8_t* ws) {
         job.shift = dp.shift;
         job.item_base = b->enc_items;
         b->enc_items += static_cast<long long>(it.f.n) * it.f.h * (dp.w_pad / 16);
-        b->jobs.push_back(job);
         DirectProblemDev d;
         int rc = MORPH_OK;
         direct_fill_problem(dp, &d, ws + it.planes_off, it.out, it.cnt, b->total_tiles, &rc);
         if (rc) return rc;
         direct_fill_band(&d, &it.f, reinterpret_cast<DirectBand*>(ws + it.band_off));
+        job.lev_range = d.lev_range;      // written by the band range kernel before the encoder runs
+        b->jobs.push_back(job);
         b->total_tiles += dp.tiles;
         b->probs.push_back(d);
     }
@@ -208,8 +209,7 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
     }
     if (!b->direct_order.empty()) {
         EncodeJob* d_jobs = reinterpret_cast<EncodeJob*>(ws + b->jobs_off);
-        int rc = launch_encode(ctx, b->jobs.data(), static_cast<int>(b->jobs.size()), b->enc_items, d_jobs, st);
-        if (rc) return rc;
+        int rc = MORPH_OK;
         DirectLaunch dl;
         std::memset(static_cast<void*>(&dl), 0, sizeof(dl));
         dl.many = reinterpret_cast<const DirectProblemDev*>(ws + b->probs_off);
@@ -241,6 +241,11 @@ int batch_enqueue(morph_batch* b, uint8_t* ws, cudaStream_t st) {
                 dl.next_unit = direct_unit_counter(reinterpret_cast<DirectBand*>(ws + it.band_off), &it.f);
             }
         rc = launch_band(ctx, dl, win, slabs, st);
+        if (rc) return rc;
+        // the planes after the bands: only the levels some unit's chunks read are written
+        rc = launch_band_range(ctx, dl, st);
+        if (rc) return rc;
+        rc = launch_encode(ctx, b->jobs.data(), static_cast<int>(b->jobs.size()), b->enc_items, d_jobs, st);
         if (rc) return rc;
         rc = launch_direct(ctx, dl, st, kind);
         if (rc) return rc;

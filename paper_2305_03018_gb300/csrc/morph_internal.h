@@ -43,6 +43,8 @@ struct EncodeJob {
     int w_pad;
     int shift;              // plane column of image column 0
     long long item_base;    // first work item of this job (batched launch)
+    const int* lev_range;   // nullable: planes are written for the levels r[0]..r[1] only (the rest
+                            // are never read: the direct problem's band range)
 };
 
 // Output adjustment of one pass of a composite operator, applied by the route's
@@ -85,6 +87,7 @@ struct DirectProblemDev {
     const int32_t* out_sub;
     const int* meta;        // pass_row_begin[n_pass+1], group_w[n_pass*8], rows[...], band taps (3 ints each)
     const DirectBand* band; // per unit; nullptr: every level, ceil(L / Lc) chunks
+    int* lev_range;         // with band: [lowest, highest] level any unit's chunks read (band range kernel)
     const int32_t* dev_off; // device-resident SE offsets (box order of the caller's SE), or nullptr
     int dev_reflect;        // 1: read dev_off at kh kw - 1 - t (the erosion's reflected SE)
     const void* src;        // the image (read by the band kernel)
@@ -309,6 +312,9 @@ unsigned long long* direct_unit_counter(DirectBand* band, const morph_image* f);
 // direct_band_window of the launch's problems; larger windows take a slower path);
 // slabs: the largest direct_band_slabs of the launch's problems
 int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, int slabs, cudaStream_t st);
+// after launch_band: each problem's lev_range from its units' bands (the levels the encoder must
+// write), one CTA per problem
+int launch_band_range(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st);
 int direct_band_window(const DirectProblemDev& d);
 int direct_band_slabs(const DirectProblemDev& d);   // band entries per unit (slabs of 32 image rows)
 int launch_fill_empty(morph_ctx* ctx, int32_t* out, int32_t* cnt, long long n, int value, cudaStream_t st,

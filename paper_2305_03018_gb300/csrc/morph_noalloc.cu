@@ -329,6 +329,7 @@ extern "C" int morph_run_noalloc(const morph_image* f, const morph_se* b, int op
     job.w_pad = p.w_pad;
     job.shift = 0;   // this planner shifts the tile grid by e instead
     job.item_base = 0;
+    job.lev_range = nullptr;           // no band: every level
     rc = launch_encode(&c, &job, 1, static_cast<long long>(f->n) * f->h * (p.w_pad / 16), nullptr, s);
     if (rc) return rc;
 
