@@ -559,9 +559,10 @@ def _cpu_baseline(args, probs, outs):
 def _extra_configs(ctx, args):
     """The largest single-GPU configuration (4096x4096, L = 256, 31x31 convex
     SE, offsets U[0, 15]: every exact form, each with its measured max count
-    error) and the 512-problem uneven batch (AUTO, one captured graph), each
-    timed for a few steps with CUDA events; every form's output is compared
-    with the FP8 route's."""
+    error), the smallest (256x256, L = 16, 7x7), the 512-problem uneven batch
+    (AUTO, one captured graph) and the learnable layer, each timed for a few
+    steps with CUDA events; every form's output is compared with the FP8
+    route's."""
     import torch
 
     from paper_2305_03018_gb300 import workloads as wl
@@ -630,6 +631,33 @@ def _extra_configs(ctx, args):
     res["c3_4096x4096_L256"] = c3
     del f, ref
     torch.cuda.empty_cache()
+    # ---- 256 x 256, L = 16, 7x7: the smallest configuration (launch-bound), every exact form and AUTO
+    q = wl.c1_small_dilation()
+    f1 = torch.from_numpy(q.f).cuda()
+    c1 = {"workload": "256x256 L=16, 7x7 SE (random 50% support) offsets U[0,3], dilation", "forms": {}}
+    ref1 = None
+    for name in ("direct_fp8", "auto", "ntt", "fft_f32", "fft_f64"):
+        try:
+            o1, n1 = ctx.dilate(f1, q.L, q.se, method=name, count=True)
+        except Exception as e:
+            c1["forms"][name] = {"value": None, "note": str(e)[:120]}
+            continue
+        torch.cuda.synchronize()
+        ctx.check()
+        if ref1 is None:
+            ref1 = (o1, n1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            ctx.dilate(f1, q.L, q.se, method=name, out=o1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.check()
+        ms = e0.elapsed_time(e1) / 20
+        c1["forms"][name] = {"value": q.f.size / (ms * 1e-3) / 1e6, "ms_per_op": ms,
+                             "exact_vs_fp8": bool(torch.equal(o1, ref1[0])) and bool(torch.equal(n1, ref1[1]))}
+    res["c1_256x256_L16"] = c1
+    del f1, ref1
     # ---- 512 uneven problems, AUTO routes, one captured graph
     probs = wl.c5_batch()
     items, pxs = [], 0

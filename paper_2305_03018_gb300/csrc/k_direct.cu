@@ -159,6 +159,25 @@ __device__ __forceinline__ int direct_pass_chunks(const DirectProblemDev* P, con
     return (b.hi - max(lo, 0)) / P->Lc + 1;
 }
 
+// The unit the producer takes next.  With the launch's counter, claims run over 2 T indices (T
+// units): index c < T offers unit c to a first round that takes the units of two or more
+// accumulations, index c >= T offers unit c - T to a second round that takes the rest, so the
+// long units go first and the launch ends on short ones.  Each CTA's first index is its own;
+// later ones come from the counter.  Returns -1 when the indices are used up.
+__device__ long long direct_claim(const DirectLaunch& dl, long long c) {
+    const long long T = dl.total_tiles;
+    while (c < 2 * T) {
+        const long long t = c < T ? c : c - T;
+        const DirectProblemDev* P = direct_find(dl, t);
+        const DirectBand bd = direct_band(P, t);
+        int n = 0;
+        for (int p = 0; p < P->n_pass && n < 2; ++p) n += direct_pass_chunks(P, bd, p);
+        if ((c < T) == (n >= 2)) return t;
+        c = static_cast<long long>(gridDim.x) + static_cast<long long>(atomicAdd(dl.next_unit, 1ull));
+    }
+    return -1;
+}
+
 __device__ __forceinline__ bool epi_any_failed(bool failed) {
     uint32_t any;
     asm volatile(
@@ -246,11 +265,11 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
         const uint32_t ring0 = smem_u32(base);
         uint32_t it = 0;
         bool ok = true;
-        // units: each CTA's first is its index, later ones are claimed from the launch's counter
-        // (in launch order where there is none); each is published to the MMA issuer and the
+        // units: claimed from the launch's counter (direct_claim), or CTA b takes units b,
+        // b + grid, ... where there is none; each is published to the MMA issuer and the
         // epilogue through the unit queue, and -1 ends their loops
         uint32_t uq = 0;
-        long long t = blockIdx.x;
+        long long t = dl.next_unit != nullptr ? direct_claim(dl, blockIdx.x) : static_cast<long long>(blockIdx.x);
         while (ok) {
             {
                 const uint32_t qs = uq % kUnitQ, qph = (uq / kUnitQ) & 1u;
@@ -258,11 +277,12 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                     ok = false;
                     break;
                 }
-                tail->unit[qs] = t < dl.total_tiles ? t : -1;
+                if (t >= dl.total_tiles) t = -1;
+                tail->unit[qs] = t;
                 mbar_arrive(smem_u32(&tail->ufull[qs]));
                 ++uq;
             }
-            if (t >= dl.total_tiles) break;
+            if (t < 0) break;
             const DirectProblemDev* P = direct_find(dl, t);
             if (dl.many != nullptr) {
                 tma_fence_acquire_desc(&P->tmA);
@@ -298,8 +318,9 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 }
               }
             }
-            t = dl.next_unit != nullptr ? static_cast<long long>(gridDim.x) + static_cast<long long>(atomicAdd(dl.next_unit, 1ull))
-                                        : t + gridDim.x;
+            t = dl.next_unit != nullptr
+                    ? direct_claim(dl, static_cast<long long>(gridDim.x) + static_cast<long long>(atomicAdd(dl.next_unit, 1ull)))
+                    : t + gridDim.x;
         }
         // drain, on every exit: the copies already issued land before the CTA may exit, also when
         // another role gave up while this loop ran to its end (in the normal course they have
