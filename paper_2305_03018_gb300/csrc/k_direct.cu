@@ -517,7 +517,10 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                 // (max, sum-at-max) over the groups of tile tt, merged with the earlier unit passes;
                 // group gg's degree of the chunk's level k is lev0 + k + its offset
                 const int pairs = rows_n * J;
-                const int* gwp = gw + p * 8;
+                // the groups' degree bases of this chunk, read once (not per pixel quad)
+                int dbase[8];
+#pragma unroll
+                for (int gg = 0; gg < 8; ++gg) dbase[gg] = gg < G ? lev0 - 1 + gw[p * 8 + gg] : 0;
                 const bool packed = Lc == kDirectLcNarrow;
                 // quads of four pixels of one row per thread and step: one 16-byte shared load per
                 // group, 16-byte output stores where the row allows them
@@ -529,10 +532,12 @@ __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_c
                         const int p0 = qd << 2;
                         const int tr = p0 >> jsh, jl = p0 & (J - 1);
                         int best[4] = {-1, -1, -1, -1}, bc[4] = {0, 0, 0, 0};
-                        for (int gg = 0; gg < G; ++gg) {
+#pragma unroll
+                        for (int gg = 0; gg < 8; ++gg) {
+                            if (gg >= G) break;
                             const uint4 e4 = *reinterpret_cast<const uint4*>(red + rbase + tr * 128 + gg * J + jl);
                             const uint32_t ev[4] = {e4.x, e4.y, e4.z, e4.w};
-                            const int d0 = lev0 - 1 + gwp[gg];
+                            const int d0 = dbase[gg];
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
                                 if (ev[c] == 0u) continue;
