@@ -138,7 +138,8 @@ typedef struct {
     int level_chunks;        /* direct route: chunks of grey levels (4, 8 or 16 levels each) a
                                 unit contracts when its band holds every level (est_flop counts
                                 that many); a unit's band usually needs fewer */
-    int ring_stages;         /* direct route: stages of the kernel's shared-memory operand ring */
+    int ring_stages;         /* direct route: stages of the kernel's shared-memory operand ring (4 for
+                                one-tile units, 3 when units hold two tiles) */
     int unit_queue;          /* direct route: units the kernel's producer may publish ahead of
                                 its MMA issuer and epilogue */
 } morph_plan_info;
@@ -349,10 +350,21 @@ int morph_mma_count(morph_ctx *ctx, uint64_t *out);
 /* Multiply-adds of the contraction the FP8 route's units needed -- for each
  * unit and offset-group pass, the pass's taps x the grey levels of its band x
  * the unit's pixels (Step 2 restricted to the degrees Step 3 can read) --
- * summed on the device by the band kernel over the calls through this context
- * (host-resident SEs with L > 16; a measurement hook, the method's own work
- * for the roofline).  Synchronises the device; *out receives the sum. */
+ * summed on the device by the direct kernel's epilogue over the calls through
+ * this context (host-resident SEs with L > 16; a measurement hook, the
+ * method's own work for the roofline).  Synchronises the device; *out
+ * receives the sum. */
 int morph_band_work(morph_ctx *ctx, uint64_t *out);
+
+/* Measurement hook: the rate, in TFLOP/s, of the tensor-core instruction the
+ * FP8 route issues (tcgen05.mma kind::f8f6f4, M = 128, N = 256, K = 32, FP32
+ * accumulation) when every SM issues it back to back from shared memory, with
+ * no copies and no waits: the tensor pipe's FP8 peak on this GPU at its
+ * present clock (about 1 ms of device time, on a stream of its own; blocks
+ * until done).  Its wait for the MMAs is bounded: a tensor pipe that does not
+ * finish raises MORPH_E_TIMEOUT through morph_stream_check.  *tflops
+ * receives the rate. */
+int morph_tc_fp8_peak(morph_ctx *ctx, double *tflops);
 
 /* Per-kernel device time, summed over the launches recorded while profiling
  * was on. */

@@ -127,6 +127,7 @@ _SIGS = {
     "morph_mma_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "morph_ctx_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "morph_band_work": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "morph_tc_fp8_peak": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "morph_run_noalloc": (ctypes.c_int, [ctypes.POINTER(morph_image), ctypes.POINTER(morph_se), ctypes.c_int, _P, _P,
                                          _P, _P]),
     "morph_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -320,6 +321,12 @@ def morph_mma_count(ctx) -> int:
     v = ctypes.c_uint64(0)
     check(load_library().morph_mma_count(ctx, ctypes.byref(v)), "morph_mma_count")
     return int(v.value)
+
+
+def morph_tc_fp8_peak(ctx) -> float:
+    v = ctypes.c_double(0.0)
+    check(load_library().morph_tc_fp8_peak(ctx, ctypes.byref(v)), "morph_tc_fp8_peak")
+    return float(v.value)
 
 
 def morph_run_noalloc(image, se, op, out_ptr, cnt_ptr, status_ptr, stream) -> int:
@@ -620,6 +627,10 @@ class Context:
     def mma_count(self) -> int:
         """tcgen05 MMAs the FP8 direct route issued through this context (synchronises)."""
         return morph_mma_count(self.handle)
+
+    def tc_fp8_peak(self) -> float:
+        """TFLOP/s of back-to-back FP8 tcgen05 MMAs on every SM (the tensor pipe's peak)."""
+        return morph_tc_fp8_peak(self.handle)
 
     def profile(self, on: bool):
         check(morph_profile_enable(self.handle, on), "morph_profile_enable")
