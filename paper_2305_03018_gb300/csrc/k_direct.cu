@@ -58,12 +58,22 @@
 
 namespace morph {
 
-constexpr int kStages = 3;
 constexpr int kStageA = 128 * 128;             // 16 KB: 128 Toeplitz rows x 128 B of K
 constexpr int kStageB = kDirectN * 128;        // 32 KB: 256 (row, level) rows x 128 B of K
 constexpr int kStageBytes = kStageA + kStageB;
-constexpr int kRedEntries = 2 * 64 * 128;      // rows_n x 128 lanes per tile, 4 B each: both tiles of a
-                                               // two-tile unit are read out before either is reduced
+constexpr int kStagesMax = 4;
+
+// Shared memory per unit kind TT (see k_direct_fp8): one-tile units (TT = 1) read one accumulator
+// at a time, so `red` holds one tile's lane results (rows_n <= 64 x 128 lanes) and the ring takes
+// a fourth stage; launches with two-tile units keep both tiles' results (both accumulators are
+// read out before either is reduced) and three stages.  A stage of the disk's 190-byte K window
+// carries 4 or 2 MMAs, and the commit-to-refill round trip of a stage (about 1700 cycles) needs
+// that much MMA work queued behind it.
+template <int TT>
+struct DirectCfg {
+    static constexpr int stages = TT == 1 ? 4 : 3;
+    static constexpr int red = TT == 1 ? 64 * 128 : 2 * 64 * 128;   // 32-bit entries
+};
 constexpr int kRunEntries = 4096;              // rows_n x J x T (int2: <= 32 x 128, or 16 x 128 x 2)
 constexpr int kRunPacked = 2 * kRunEntries;    // the same as packed uint32 entries (4-level plans: 64 x 128)
 constexpr int kRunWords = kRunPacked / 128;    // 32-bit words of running results per epilogue thread
@@ -74,8 +84,8 @@ constexpr uint32_t kTmemCols = 2 * kDirectN;   // two accumulators
 constexpr int kUnitQ = 4;                      // units the producer may publish ahead of the consumers
 
 struct DirectSmemTail {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
+    uint64_t full[kStagesMax];
+    uint64_t empty[kStagesMax];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint64_t ufull[kUnitQ];                    // unit queue: published by the producer
@@ -86,10 +96,11 @@ struct DirectSmemTail {
     int abort;
 };
 
-int direct_stages() { return kStages; }
+int direct_stages(int unit_tiles) { return unit_tiles == 1 ? DirectCfg<1>::stages : DirectCfg<2>::stages; }
 int direct_unit_queue() { return kUnitQ; }
-int direct_smem_bytes(int stages) {
-    return 1024 + stages * kStageBytes + kRedEntries * 4 + static_cast<int>(sizeof(DirectSmemTail));
+template <int TT>
+int direct_smem_bytes() {
+    return 1024 + DirectCfg<TT>::stages * kStageBytes + DirectCfg<TT>::red * 4 + static_cast<int>(sizeof(DirectSmemTail));
 }
 
 __device__ __forceinline__ const DirectProblemDev* direct_find(const DirectLaunch& dl, long long t) {
@@ -222,6 +233,8 @@ __device__ __forceinline__ void epi_read_rows(uint32_t trow, uint32_t* red_m) {
 // issue loop); TT = 0: read the kind per problem.
 template <int TT>
 __global__ void __launch_bounds__(kDirectThreads, 1) k_direct_fp8(const __grid_constant__ DirectLaunch dl) {
+    constexpr int kStages = DirectCfg<TT>::stages;
+    constexpr int kRedEntries = DirectCfg<TT>::red;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     // red: one lane's result of one image row of one chunk (epi_read_rows)
@@ -1460,21 +1473,20 @@ int launch_band_range(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st) {
 
 int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_kind) {
     if (dl.total_tiles <= 0) return MORPH_OK;
-    const int smem = direct_smem_bytes(kStages);
     if (!kernels_ready(ctx->device, kGroupDirect)) {
-        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, direct_smem_bytes<0>()));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, direct_smem_bytes<1>()));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, direct_smem_bytes<2>()));
+        MORPH_CUDA_TRY(cudaFuncSetAttribute(k_direct_fp8<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, direct_smem_bytes<3>()));
         mark_kernels_ready(ctx->device, kGroupDirect);
     }
     const int kind = dl.many == nullptr ? direct_kind(dl.single) : (uniform_kind < 0 ? 0 : uniform_kind);
     long long grid = dl.total_tiles < ctx->num_sms ? dl.total_tiles : ctx->num_sms;
     prof_begin(ctx, st, "k_direct_fp8");
-    if (kind == 1) k_direct_fp8<1><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
-    else if (kind == 2) k_direct_fp8<2><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
-    else if (kind == 3) k_direct_fp8<3><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
-    else k_direct_fp8<0><<<static_cast<unsigned>(grid), kDirectThreads, smem, st>>>(dl);
+    if (kind == 1) k_direct_fp8<1><<<static_cast<unsigned>(grid), kDirectThreads, direct_smem_bytes<1>(), st>>>(dl);
+    else if (kind == 2) k_direct_fp8<2><<<static_cast<unsigned>(grid), kDirectThreads, direct_smem_bytes<2>(), st>>>(dl);
+    else if (kind == 3) k_direct_fp8<3><<<static_cast<unsigned>(grid), kDirectThreads, direct_smem_bytes<3>(), st>>>(dl);
+    else k_direct_fp8<0><<<static_cast<unsigned>(grid), kDirectThreads, direct_smem_bytes<0>(), st>>>(dl);
     prof_end(ctx, st);
     ctx->launches += 1;
     MORPH_CUDA_TRY(cudaGetLastError());

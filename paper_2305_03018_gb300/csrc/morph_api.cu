@@ -752,7 +752,7 @@ int morph_plan_query(morph_ctx* ctx, const morph_image* f, const morph_se* b, in
         out->method = MORPH_DIRECT_FP8;
         out->k_steps = d.ksteps;
         out->level_chunks = (d.L + d.Lc - 1) / std::max(1, d.Lc);
-        out->ring_stages = direct_stages();
+        out->ring_stages = direct_stages(d.T);
         out->unit_queue = direct_unit_queue();
         out->groups = d.G;
         out->passes = d.n_pass;

@@ -290,7 +290,7 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
 int direct_kind(const DirectProblemDev& d);
 int launch_direct(morph_ctx* ctx, const DirectLaunch& dl, cudaStream_t st, int uniform_kind = -1);
 int direct_smem_bytes(int stages);
-int direct_stages();
+int direct_stages(int unit_tiles);   // ring depth of the direct kernel for units of that many tiles
 int direct_unit_queue();   // slots of the direct kernel's unit queue
 void direct_fill_problem(const DirectPlan& p, DirectProblemDev* d, const uint8_t* planes, int32_t* out,
                          int32_t* out_cnt, long long tile_base, int* status);

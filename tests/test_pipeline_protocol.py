@@ -21,8 +21,10 @@ import random
 
 import pytest
 
-def _ring_stages():
-    """The direct kernel's ring depth as the library reports it (host-only plan query)."""
+def _ring_stages(kw=3, L=16, side=64, levels=1):
+    """The direct kernel's ring depth as the library reports it (host-only plan query) for a
+    kw x kw SE with `levels` offset levels: two-tile units for a small SE with several levels,
+    one-tile units for a wide flat one."""
     import ctypes
 
     import numpy as np
@@ -33,18 +35,28 @@ def _ring_stages():
     im = M.morph_image()
     im.data = ctypes.addressof(buf)
     im.dtype = M.MORPH_U8
-    im.n, im.h, im.w, im.row_stride, im.batch_stride, im.L = 1, 64, 64, 64, 64 * 64, 16
-    sv = M.se_view(wl.se_flat_square(3))
-    return M.morph_plan_query(None, im, sv.c, 0, M.make_opts("direct_fp8")).ring_stages
+    im.n, im.h, im.w, im.row_stride, im.batch_stride, im.L = 1, side, side, side, side * side, L
+    se = wl.se_flat_square(kw) if levels == 1 else wl.se_full_random(wl.rng(1), kw, levels - 1)
+    sv = M.se_view(se)
+    info = M.morph_plan_query(None, im, sv.c, 0, M.make_opts("direct_fp8"))
+    return info.ring_stages, info.unit_tiles
 
 
 _STAGES = []
 
 
-def _stages():
+def _stage_depths():
+    """The ring depths of the kernel's unit kinds (two-tile and one-tile units)."""
     if not _STAGES:
-        _STAGES.append(_ring_stages())
-    return _STAGES[0]
+        d2, t2 = _ring_stages(9, 64, 256, levels=8)
+        d1, t1 = _ring_stages(63, 64, 2048)
+        assert (t2, t1) == (2, 1)
+        _STAGES.extend(sorted({d1, d2}))
+    return list(_STAGES)
+
+
+def _stages():
+    return min(_stage_depths())
 
 
 def _unit_queue():
@@ -93,9 +105,9 @@ def test_split_schedule_covers_each_k_step_once(J):
         assert 32 * ksteps >= J + kw - 1                    # the window covers every tap column
 
 
-def _ring_model(units, seed):
+def _ring_model(units, seed, STAGES=None):
     """units: (blocks per SE row, split) per row, in launch order."""
-    STAGES = _stages()
+    STAGES = STAGES or _stages()
     rnd = random.Random(seed)
     program = [(r, kc) for r, (nb, _) in enumerate(units) for kc in range(nb)]
     slot = [None] * STAGES
@@ -155,7 +167,8 @@ def test_stage_ring_never_deadlocks_or_overwrites():
     for trial in range(150):
         units = [rnd.choice(kinds) for _ in range(rnd.randint(1, 10))]
         for seed in range(4):
-            _ring_model(units, 97 * trial + seed)
+            for depth in _stage_depths():
+                _ring_model(units, 97 * trial + seed, depth)
 
 
 def _plan(kw, nlev, h=2048, w=2048):
@@ -207,7 +220,7 @@ def test_model_matches_the_library_plan(nlev):
 
 
 # ------------------------------------------------------------------ abort path
-def _abort_model(n_units, blocks_per_unit, seed, inject_p, always_drain=True):
+def _abort_model(n_units, blocks_per_unit, seed, inject_p, always_drain=True, STAGES=None):
     """The three roles of k_direct_fp8 (one tile per unit, accumulator slots used
     alternately) with one injected wait timeout at a random blocked wait.  The
     producer publishes each unit (then -1) through the unit queue, whose slot is
@@ -216,7 +229,7 @@ def _abort_model(n_units, blocks_per_unit, seed, inject_p, always_drain=True):
     complete in issue order, each then arriving on its barrier.  Returns the
     copies and MMA batches still in flight when all roles reach the final barrier
     (after which TMEM is freed and the CTA exits), or raises on a deadlock."""
-    STAGES, Q = _stages(), _unit_queue()
+    STAGES, Q = STAGES or _stages(), _unit_queue()
     rnd = random.Random(seed)
     st = {"abort": False, "injected": False}
     landed = set()            # copy ids that have landed
@@ -354,7 +367,9 @@ def test_abort_drains_every_copy_and_mma_before_exit():
     for trial in range(600):
         n_units = 1 + trial % 9                 # up to twice the unit queue
         blocks = 1 + (trial // 9) % 4
-        copies, mmas = _abort_model(n_units, blocks, trial, inject_p=0.02)
+        for depth in _stage_depths():
+            copies, mmas = _abort_model(n_units, blocks, trial, inject_p=0.02, STAGES=depth)
+            assert copies == 0 and mmas == 0, (trial, depth, copies, mmas)
         assert copies == 0 and mmas == 0, (trial, copies, mmas)
         hits += 1
     assert hits == 600
