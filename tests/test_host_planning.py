@@ -104,3 +104,30 @@ def test_huge_offsets_plan_only_the_fp8_route():
         with pytest.raises(M.MorphError) as ei:
             _ws(im, se, 0, method)
         assert ei.value.status == M.MORPH_E_UNSUPPORTED
+
+
+def _direct_info(shape, L, se):
+    sv = M.se_view(se)
+    return M.morph_plan_query(None, _img(*shape, L), sv.c, 0, M.make_opts("direct_fp8"))
+
+
+def test_chunk_width_follows_the_plan_rules():
+    g = wl.rng(71)
+    # 16 < L <= 64, a large SE on a 2048^2 image: 4-level chunks of 64-row units
+    info = _direct_info((1, 2048, 2048), 64, wl.se_flat_disk(31))
+    assert (info.tile_h, info.level_chunks) == (64, 16)
+    # the same SE on a small image (fewer than two waves of 64-row units): 8-level chunks
+    info = _direct_info((1, 300, 300), 64, wl.se_flat_disk(31))
+    assert (info.tile_h, info.level_chunks) == (32, 8)
+    # a small SE (few MMAs per accumulation): 8-level chunks
+    info = _direct_info((1, 2048, 2048), 64, wl.se_full_random(g, 9, 7))
+    assert (info.tile_h, info.level_chunks) == (32, 8)
+    # offsets beyond 4095 - L: the packed running results could not hold the degrees
+    m = np.ones((31, 31), np.uint8)
+    off = (g.integers(0, 2, size=m.shape) * 5000).astype(np.int32)
+    info = _direct_info((1, 2048, 2048), 64, wl.SE(m, off, (15, 15), "far"))
+    assert (info.tile_h, info.level_chunks) == (32, 8)
+    # L <= 16 and L > 64: 16-level chunks of 16-row units
+    for L in (16, 256):
+        info = _direct_info((1, 2048, 2048), L, wl.se_flat_disk(31))
+        assert (info.tile_h, info.level_chunks) == (16, -(-L // 16))
