@@ -30,7 +30,10 @@
 // groups and chunks with (max, sum-at-max).
 //
 // Warp roles (192 threads, one persistent CTA per SM):
-//   warp 0   : TMA producer (one lane) -- A and B tiles into a 3-stage ring;
+//   warp 0   : TMA producer (one lane) -- claims units (a per-launch counter, units with
+//              two or more accumulations first), hands them to the other roles through a
+//              shared-memory queue, and stages A and B tiles into a 4-stage ring (3 when
+//              units hold two tiles);
 //   warp 1   : TMEM allocator + MMA issuer (one lane), tcgen05.mma kind::f8f6f4;
 //   warps 2-5: epilogue (TMEM -> registers -> SMEM reduction -> int32 output).
 // Two TMEM accumulators (2 x 256 columns) let the epilogue of one unit
@@ -74,8 +77,8 @@ struct DirectCfg {
     static constexpr int stages = TT == 1 ? 4 : 3;
     static constexpr int red = TT == 1 ? 64 * 128 : 2 * 64 * 128;   // 32-bit entries
 };
-constexpr int kRunEntries = 4096;              // rows_n x J x T (int2: <= 32 x 128, or 16 x 128 x 2)
-constexpr int kRunPacked = 2 * kRunEntries;    // the same as packed uint32 entries (4-level plans: 64 x 128)
+constexpr int kRunEntries = 4096;              // pixels per unit, rows_n x J x T, with int2 running results
+constexpr int kRunPacked = 2 * kRunEntries;    // ... with packed ones (4-level plans: 64 x 128)
 constexpr int kRunWords = kRunPacked / 128;    // 32-bit words of running results per epilogue thread
 constexpr int kDirectNarrowMinMmas = 96;       // MMAs per accumulation below which 4-level plans do not pay
 constexpr int kDirectThreads = 192;
@@ -819,7 +822,8 @@ int plan_direct_host(const morph_image* f, const morph_se* se, int erode, Direct
     const int run_cap = p->Lc == kDirectLcNarrow ? kRunPacked : kRunEntries;
     if (p->T == 1 && p->J >= 32 && f->w > p->J && 2 * p->rows_n * p->J <= run_cap) {
         // split two-tile units: fewer staged blocks per SE row for both tiles; J a multiple of 32
-        // keeps each K step inside one 128-byte row, both tiles' running pairs fit the run buffer
+        // keeps each K step inside one 128-byte row, both tiles' running results fit the epilogue
+        // threads' run words
         const int nb = (p->J + 32 * p->ksteps + 127) / 128;
         const long long units = static_cast<long long>(f->n) * p->tiles_y * ((f->w + 2 * p->J - 1) / (2 * p->J));
         if (nb < 2 * p->nk && units >= kDirectSplitMinUnits) {
