@@ -131,11 +131,16 @@ __device__ __forceinline__ TileCoord direct_tile(const DirectProblemDev* P, long
     return c;
 }
 
-// Image rows of a unit that the band kernel takes at a time: a 64-row unit
-// has two band entries, which the direct kernel combines.
-constexpr int kBandSlabRows = 32;
+// Image rows of a unit that the band kernel takes at a time: as many as give 2048 pixel pairs
+// (its largest per-CTA load: 8 pairs per thread), at most the unit's rows -- 32 for units 128
+// columns wide, 64 for 64 columns, 16 for 256; a unit with more rows has several band entries,
+// which the direct kernel combines.
+__host__ __device__ __forceinline__ int band_slab_rows(int rows_n, int uw) { return min(rows_n, 4096 / uw); }
 
-__host__ __device__ __forceinline__ int band_slabs(int rows_n) { return (rows_n + kBandSlabRows - 1) / kBandSlabRows; }
+__host__ __device__ __forceinline__ int band_slabs(int rows_n, int uw) {
+    const int r = band_slab_rows(rows_n, uw);
+    return (rows_n + r - 1) / r;
+}
 
 // The unit's level band (see DirectBand), from its slabs' entries: hi = the
 // largest level in their windows (-1: none read), lb = the smallest of their
@@ -148,7 +153,7 @@ __device__ __forceinline__ DirectBand direct_band(const DirectProblemDev* P, lon
         b.lb = -1;
         return b;
     }
-    const int ns = band_slabs(P->rows_n);
+    const int ns = band_slabs(P->rows_n, P->T * P->J);
     const DirectBand* e = P->band + (t - P->tile_base) * ns;
     b = e[0];
     for (int k = 1; k < ns; ++k) {
@@ -1295,7 +1300,7 @@ __device__ __forceinline__ int band_lower(const DirectProblemDev* P, const TileC
 }
 
 __global__ void __launch_bounds__(256, kBandCtasPerSm) k_band(const __grid_constant__ DirectLaunch dl, int win_bytes, int slabs) {
-    // One work item per unit slab (kBandSlabRows image rows of a unit; item s T + t is slab s of
+    // One work item per unit slab (band_slab_rows image rows of a unit; item s T + t is slab s of
     // unit t, T units in the launch, and units with fewer slabs skip the items past theirs).
     // The slab's input window (rows i - r + oy, columns j - c + ox over the SE box, not clipped)
     // is staged as half2 pairs q[r][k] = (level(r, k), level(r, k + s)) (band_pitch), -4096
@@ -1314,11 +1319,11 @@ __global__ void __launch_bounds__(256, kBandCtasPerSm) k_band(const __grid_const
         const int sl = static_cast<int>(it / dl.total_tiles);
         const long long t = it - sl * dl.total_tiles;
         const DirectProblemDev* P = direct_find(dl, t);
-        if (P->band == nullptr || sl >= band_slabs(P->rows_n)) continue;   // block-uniform
+        if (P->band == nullptr || sl >= band_slabs(P->rows_n, P->T * P->J)) continue;   // block-uniform
         TileCoord tc = direct_tile(P, t);
-        tc.i0 += sl * kBandSlabRows;
+        const int rows = band_slab_rows(P->rows_n, P->T * P->J);
+        tc.i0 += sl * rows;
         const int h = P->h, w = P->w, uw = P->T * P->J, ntap = min(P->n_band_taps, kBandTapsMax);
-        const int rows = min(P->rows_n, kBandSlabRows);
         const long long ibase = static_cast<long long>(tc.n) * P->batch_stride;
         const int wr0 = tc.i0 - (P->kh - 1 - P->oy), wc0 = tc.j0 - (P->kw - 1 - P->ox);
         const int WR = rows + P->kh - 1, WQ = band_pitch(uw, P->kw);
@@ -1392,18 +1397,18 @@ __global__ void __launch_bounds__(256, kBandCtasPerSm) k_band(const __grid_const
             DirectBand b;
             b.hi = hi;
             b.lb = lb;
-            const_cast<DirectBand*>(P->band)[(t - P->tile_base) * band_slabs(P->rows_n) + sl] = b;
+            const_cast<DirectBand*>(P->band)[(t - P->tile_base) * band_slabs(P->rows_n, P->T * P->J) + sl] = b;
         }
     }
 }
 
 int direct_band_window(const DirectProblemDev& d) {
     if (d.band == nullptr) return 0;
-    const long long b = static_cast<long long>(std::min(d.rows_n, kBandSlabRows) + d.kh - 1) * band_pitch(d.T * d.J, d.kw) * 4;
+    const long long b = static_cast<long long>(band_slab_rows(d.rows_n, d.T * d.J) + d.kh - 1) * band_pitch(d.T * d.J, d.kw) * 4;
     return static_cast<int>(std::min<long long>(kBandWinBytes, (b + 1023) & ~1023LL));
 }
 
-int direct_band_slabs(const DirectProblemDev& d) { return band_slabs(d.rows_n); }
+int direct_band_slabs(const DirectProblemDev& d) { return band_slabs(d.rows_n, d.T * d.J); }
 
 int launch_band(morph_ctx* ctx, const DirectLaunch& dl, int win_bytes, int slabs, cudaStream_t st) {
     if (dl.total_tiles <= 0) return MORPH_OK;
